@@ -1,0 +1,231 @@
+/*
+ * trim.h -- C ABI of the GB300 graph-trimming library.
+ *
+ * Computes the trimmed graph of Guo & Sekerinski, "Efficient Parallel Graph
+ * Trimming by Arc-Consistency" (arXiv 2107.12720): Definition 1 (the maximal
+ * subgraph in which every vertex keeps at least one out-edge) together with
+ * the peeling step of every removed vertex (Definition 2, counted from 0).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a trim_err_t; nothing aborts. A failed call leaves the
+ *    caller's output buffers untouched; trim_last_error() describes it.
+ *  - Vertex ids and CSR offsets are uint32. n <= 0xFFFFFFFE (0xFFFFFFFF is the
+ *    LIVE sentinel of trim_level), m < 2^32.
+ *  - Device pointers passed in are BORROWED: they must stay valid and unchanged
+ *    until trim_destroy(). Host pointers are copied during the call.
+ *  - A context is bound to one CUDA stream and to the device current at
+ *    trim_create(); it is not thread-safe. All device work is ordered on that
+ *    stream.
+ *  - trim_run() is repeatable: it resets all state, and repeated calls give
+ *    bit-identical status and level, whatever variant or schedule is used.
+ *  - Nothing here calls into any CPU implementation of the method: if the
+ *    device or the kernels are unavailable, calls fail with TRIM_ERR_CUDA or
+ *    TRIM_ERR_NO_DEVICE.
+ */
+#ifndef TRIM_H_
+#define TRIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRIM_LIVE 0xFFFFFFFFu
+
+typedef enum {
+  TRIM_OK = 0,
+  TRIM_ERR_INVALID_ARG = 1, /* null pointer, size mismatch, unknown enum value       */
+  TRIM_ERR_BAD_GRAPH = 2,   /* offsets not monotone, target >= n, csr_in not G^T ... */
+  TRIM_ERR_TOO_LARGE = 3,   /* n or m beyond the uint32 limits above                  */
+  TRIM_ERR_OOM = 4,         /* device allocation failed (or the memory cap was hit)   */
+  TRIM_ERR_CUDA = 5,        /* a CUDA runtime call failed                             */
+  TRIM_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out (see spin_limit_ns) */
+  TRIM_ERR_STATE = 7,       /* call out of order (e.g. trim_status before trim_run)   */
+  TRIM_ERR_NO_DEVICE = 8    /* no CUDA device, or not an sm_103 device                */
+} trim_err_t;
+
+/* Per-round kernel choice.
+ *  TRIM_AC4_PUSH     Section 5, Algorithm 6: out-degree counters decremented through
+ *                    the transposed graph G^T (needs csr_in or builds it on device).
+ *  TRIM_AC6_SUPPORT  Section 6, Algorithms 7-8 and Definition 3: one support per
+ *                    vertex (edge_index) and supporting sets S; no G^T needed.
+ *  TRIM_AC3_PULL     Section 4, Algorithm 4 with the edge_index jump of Section 8:
+ *                    a sweep over the vertices still live.
+ *  TRIM_SCHED_*      choose one of the three per round on the device:
+ *    HEURISTIC       a fixed cost rule on frontier and live-set sizes;
+ *    LEARNED         the scheduler MLP set by trim_set_model (falls back to the
+ *                    heuristic outside the model's training range or without model);
+ *    SCRIPTED        the per-round list given to trim_set_schedule.
+ * Every choice yields the same status and level. */
+typedef enum {
+  TRIM_AC4_PUSH = 0,
+  TRIM_AC6_SUPPORT = 1,
+  TRIM_AC3_PULL = 2,
+  TRIM_SCHED_HEURISTIC = 3,
+  TRIM_SCHED_LEARNED = 4,
+  TRIM_SCHED_SCRIPTED = 5
+} trim_variant_t;
+
+/* A graph in CSR form (Section 2.1 "Graph Storage"): the successors of v are
+ * targets[offsets[v] .. offsets[v+1]). offsets has n+1 entries with offsets[0]=0
+ * and offsets[n]=m; every target is < n. Successor order is free; duplicate
+ * edges and self-loops are allowed (a self-loop keeps its vertex LIVE). */
+typedef struct {
+  uint32_t n;
+  uint64_t m;
+  const uint32_t* offsets;
+  const uint32_t* targets;
+  int on_device; /* 1: device pointers (borrowed); 0: host pointers (copied) */
+} trim_csr_t;
+
+/* flags of trim_create */
+#define TRIM_FLAG_VALIDATE 0x1u  /* check the CSR (and that csr_in is its transpose) on device */
+#define TRIM_FLAG_STATS 0x2u     /* count edges inspected, atomics, candidates per run          */
+#define TRIM_FLAG_ROUND_LOG 0x4u /* record per-round features and device timestamps            */
+
+/* Tunables (filled by the autotuner; defaults are sensible). */
+typedef struct {
+  uint32_t block_threads;     /* threads per CTA of the persistent kernel (128..1024, x32) */
+  uint32_t ctas_per_sm;       /* persistent CTAs per SM (0 = as many as fit)               */
+  uint32_t big_degree;        /* AC-4: in-degree above which a vertex is split into pieces  */
+  uint32_t piece_edges;       /* AC-4: edges per piece of a big vertex                      */
+  uint32_t batch_cta_max_n;   /* batched: graphs with at most this many vertices run in
+                                 one CTA (0 = never)                                         */
+  uint32_t batch_cta_max_m;   /* batched: ... and at most this many edges                   */
+  uint64_t spin_limit_ns;     /* bound of every device-side wait; past it the run stops
+                                 with TRIM_ERR_TIMEOUT                                       */
+  float heur_push_ratio;      /* heuristic: push while sum(indeg F) < ratio * n_live        */
+  float heur_ac6_ratio;       /* heuristic (no G^T): AC-6 while |F| < ratio * n_live        */
+} trim_params_t;
+
+/* Statistics of the last run (sizes in vertices/edges, times in ms). */
+typedef struct {
+  uint32_t rounds;          /* alpha: number of peeling steps that removed something      */
+  uint32_t n_dead;          /* vertices removed                                          */
+  float device_ms;          /* trim time between events around the device work          */
+  uint64_t edges_inspected; /* TRIM_FLAG_STATS: out-edges read by AC-6/AC-3 scans         */
+  uint64_t in_edges_pushed; /* TRIM_FLAG_STATS: in-edges walked by AC-4 (atomics issued)   */
+  uint64_t candidates;      /* TRIM_FLAG_STATS: AC-6 supporting-set members re-scanned     */
+  uint64_t live_swept;      /* TRIM_FLAG_STATS: AC-3 live-list entries visited             */
+  uint32_t rounds_by_variant[3]; /* rounds run by AC-4, AC-6, AC-3                         */
+  uint32_t reserved;
+} trim_run_stats_t;
+
+/* One record per round of a TRIM_FLAG_ROUND_LOG run. features[] are the
+ * scheduler inputs computed before the round (see trim_features_doc). */
+typedef struct {
+  uint32_t round;        /* r: the round that removes the vertices of level r          */
+  uint32_t variant;      /* trim_variant_t actually run (0..2)                        */
+  uint32_t frontier;     /* |F_{r-1}|                                                 */
+  uint32_t removed;      /* |F_r|                                                     */
+  uint64_t t_start_ns;   /* device %globaltimer at the start of the round              */
+  uint64_t t_end_ns;     /* ... at its end (after the grid-wide barrier)               */
+  float features[12];
+} trim_round_rec_t;
+
+typedef struct trim_ctx trim_ctx;
+
+/* Creates a context for G (csr_out) and optionally G^T (csr_in, may be NULL).
+ * csr_in, when given, must be the transpose of csr_out (same n and m; checked
+ * when TRIM_FLAG_VALIDATE is set); without it the AC-4 variant builds G^T on the
+ * device on first use (a counting sort; its time is not part of trim_run).
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * On success *out receives the context. Allocates device memory ~ (40 n + 4 m) B. */
+trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void* cuda_stream,
+                       uint32_t flags, trim_ctx** out);
+
+/* Runs the whole trimming (all rounds) with the given variant or scheduler.
+ * Returns once status/level are final on the device. stats may be NULL. */
+trim_err_t trim_run(trim_ctx* ctx, trim_variant_t variant, trim_run_stats_t* stats);
+
+/* Enqueues the same work as trim_run without waiting (no host synchronisation,
+ * so it may be captured into a CUDA graph). Errors raised on the device surface
+ * at the next trim_sync(). */
+trim_err_t trim_run_async(trim_ctx* ctx, trim_variant_t variant);
+/* Waits for the enqueued work and reports its device-side status; stats may be NULL. */
+trim_err_t trim_sync(trim_ctx* ctx, trim_run_stats_t* stats);
+
+/* Output of the last run: out[v] = 1 if v is LIVE (Definition 1), 0 if removed.
+ * out has n bytes, on the device if out_on_device else on the host. */
+trim_err_t trim_status(const trim_ctx* ctx, uint8_t* out, int out_on_device);
+
+/* Output of the last run: out[v] = the peeling step that removed v (0 for a vertex
+ * without out-edges; else 1 + the largest level among its successors, i.e. the
+ * length of its longest path to a sink), or TRIM_LIVE. n uint32 values. */
+trim_err_t trim_level(const trim_ctx* ctx, uint32_t* out, int out_on_device);
+
+/* Device pointer to the context's level array (n uint32, valid until the next
+ * run or trim_destroy): lets callers read results without a copy. */
+trim_err_t trim_level_device_ptr(const trim_ctx* ctx, const uint32_t** out);
+
+/* Batched trimming of G independent graphs packed into the context's CSR:
+ * graph g owns vertices [graph_off[g], graph_off[g+1]) and no edge may cross two
+ * graphs (checked with TRIM_FLAG_VALIDATE). graph_off: G+1 host uint32 values,
+ * graph_off[0]=0, graph_off[G]=n. Graphs small enough (trim_params_t
+ * batch_cta_max_n / _m) are trimmed whole inside one CTA each; the rest join a
+ * grid-wide round loop run with `variant`. Results equal trimming each graph
+ * alone (and the union at once): read them with trim_status / trim_level. */
+trim_err_t trim_batch_run(trim_ctx* ctx, const uint32_t* graph_off, uint32_t G,
+                          trim_variant_t variant, trim_run_stats_t* stats);
+
+trim_err_t trim_set_params(trim_ctx* ctx, const trim_params_t* params);
+trim_err_t trim_get_params(const trim_ctx* ctx, trim_params_t* params);
+/* Default tunables for the current device (no context needed). */
+trim_err_t trim_default_params(trim_params_t* params);
+
+/* Scheduler MLP (12 -> 32 -> 32 -> 3, ReLU), TRIM_MLP_NPARAMS fp32 values laid
+ * out as W1[32][12] b1[32] W2[32][32] b2[32] W3[3][32] b3[3], followed by the
+ * input normalisation mean[12], inv_std[12] and the training range lo[12],
+ * hi[12] (TRIM_MLP_NBLOB floats in all). Host pointer, copied. */
+#define TRIM_MLP_NIN 12
+#define TRIM_MLP_NH 32
+#define TRIM_MLP_NOUT 3
+#define TRIM_MLP_NPARAMS 1571
+#define TRIM_MLP_NBLOB (TRIM_MLP_NPARAMS + 4 * TRIM_MLP_NIN)
+trim_err_t trim_set_model(trim_ctx* ctx, const float* blob, size_t n_floats);
+
+/* Per-round variant list for TRIM_SCHED_SCRIPTED (host pointer, copied): round r
+ * (1-based) runs variants[(r-1) % len]; each entry 0..2. */
+trim_err_t trim_set_schedule(trim_ctx* ctx, const uint8_t* variants, uint32_t len);
+
+/* Copies up to cap records of the last TRIM_FLAG_ROUND_LOG run to out (host). */
+trim_err_t trim_get_round_log(const trim_ctx* ctx, trim_round_rec_t* out, size_t cap,
+                              size_t* n_out);
+
+void trim_destroy(trim_ctx* ctx);
+
+/* Process-wide cap on the device bytes one context may allocate (0 = no cap).
+ * Allocations past it fail with TRIM_ERR_OOM, which lets callers (and tests)
+ * exercise out-of-memory paths without exhausting the device. */
+trim_err_t trim_set_alloc_limit(uint64_t bytes);
+
+/* Message of the last failed call on ctx (or of the last failed trim_create when
+ * ctx is NULL). Never NULL. */
+const char* trim_last_error(const trim_ctx* ctx);
+
+/* ---- scheduler MLP training kernels (plain fp32, no tensor cores) ----
+ * All pointers are DEVICE pointers; work is enqueued on cuda_stream.
+ * X: [N][12] fp32 features, y: [N] uint8 labels in 0..2,
+ * params: TRIM_MLP_NPARAMS fp32 (layout above, without the normalisation tail;
+ * inputs are used as given).
+ *
+ * trim_mlp_forward: logits[N][3].
+ * trim_mlp_loss_grad: mean softmax cross-entropy over the N rows into *loss
+ *   (device float) and its gradient w.r.t. params into grad (TRIM_MLP_NPARAMS).
+ *   scratch: device buffer of at least trim_mlp_scratch_bytes(N) bytes.
+ * trim_mlp_adam_step: one Adam update (Kingma & Ba, 2015) of params from grad;
+ *   m, v: TRIM_MLP_NPARAMS fp32 moment buffers; t: the 1-based step number. */
+size_t trim_mlp_scratch_bytes(uint32_t N);
+trim_err_t trim_mlp_forward(const float* params, const float* X, uint32_t N, float* logits,
+                            void* cuda_stream);
+trim_err_t trim_mlp_loss_grad(const float* params, const float* X, const uint8_t* y, uint32_t N,
+                              float* loss, float* grad, void* scratch, void* cuda_stream);
+trim_err_t trim_mlp_adam_step(float* params, const float* grad, float* m, float* v, uint32_t t,
+                              float lr, float beta1, float beta2, float eps, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRIM_H_ */

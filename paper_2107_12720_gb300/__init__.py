@@ -1,0 +1,159 @@
+"""Python binding of the GB300 graph-trimming library (include/trim.h).
+
+Argument marshalling only: every step of the trimming runs in the CUDA kernels
+of ``libtrim.so``. There is no CPU fallback; if the library is missing or no
+sm_103 device is present, calls raise ``TrimError``.
+
+Low-level functions carry the C names (``trim_create``, ``trim_run``,
+``trim_status``, ``trim_level``, ``trim_batch_run``, ...). ``Trimmer`` wraps a
+context for use with torch tensors (device memory and streams come from torch).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .abi import (LIB_PATH, TRIM_AC3_PULL, TRIM_AC4_PUSH, TRIM_AC6_SUPPORT, TRIM_FLAG_ROUND_LOG,
+                  TRIM_FLAG_STATS, TRIM_FLAG_VALIDATE, TRIM_LIVE, TRIM_MLP_NBLOB,
+                  TRIM_MLP_NPARAMS, TRIM_SCHED_HEURISTIC, TRIM_SCHED_LEARNED,
+                  TRIM_SCHED_SCRIPTED, TrimCsr, TrimError, TrimParams, TrimRoundRec,
+                  TrimRunStats, lib, check)
+from .abi import (trim_batch_run, trim_create, trim_default_params, trim_destroy,
+                  trim_get_params, trim_get_round_log, trim_last_error, trim_level,
+                  trim_level_device_ptr, trim_mlp_adam_step, trim_mlp_forward, trim_mlp_loss_grad,
+                  trim_mlp_scratch_bytes, trim_run, trim_run_async, trim_set_alloc_limit,
+                  trim_set_model, trim_set_params, trim_set_schedule, trim_status, trim_sync)
+
+VARIANTS = {"ac4": TRIM_AC4_PUSH, "ac6": TRIM_AC6_SUPPORT, "ac3": TRIM_AC3_PULL,
+            "heuristic": TRIM_SCHED_HEURISTIC, "learned": TRIM_SCHED_LEARNED,
+            "scripted": TRIM_SCHED_SCRIPTED}
+
+__all__ = ["Trimmer", "TrimError", "VARIANTS", "lib", "LIB_PATH"]
+
+
+def _variant(v) -> int:
+    if isinstance(v, str):
+        return VARIANTS[v]
+    return int(v)
+
+
+class Trimmer:
+    """One trimming context over a CSR graph.
+
+    ``off``/``tgt`` (and optionally ``off_in``/``tgt_in`` for G^T) are uint32
+    arrays: CUDA torch tensors are borrowed (kept alive by this object), numpy
+    arrays or CPU tensors are copied to the device by the library.
+    """
+
+    def __init__(self, off, tgt, off_in=None, tgt_in=None, stream=None, flags: int = 0):
+        import torch
+        self._keep = []
+        out_csr = self._csr(off, tgt)
+        in_csr = self._csr(off_in, tgt_in) if off_in is not None else None
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+        self.ctx = trim_create(out_csr, in_csr, sp, flags)
+        self.n = out_csr.n
+        self.m = out_csr.m
+        self.flags = flags
+
+    def _csr(self, off, tgt):
+        import torch
+        if isinstance(off, torch.Tensor) and off.is_cuda:
+            off = off.contiguous()
+            tgt = tgt.contiguous()
+            if off.dtype not in (torch.int32, torch.uint32) or tgt.dtype not in (torch.int32,
+                                                                                   torch.uint32):
+                raise TrimError(1, "CSR tensors must be 32-bit integers")
+            self._keep += [off, tgt]
+            return TrimCsr(off.numel() - 1, tgt.numel(), off.data_ptr(),
+                           tgt.data_ptr() if tgt.numel() else None, 1)
+        if isinstance(off, torch.Tensor):
+            off = off.numpy()
+            tgt = tgt.numpy()
+        off = np.ascontiguousarray(off, np.uint32)
+        tgt = np.ascontiguousarray(tgt, np.uint32)
+        self._keep += [off, tgt]
+        return TrimCsr(off.shape[0] - 1, tgt.shape[0], off.ctypes.data,
+                       tgt.ctypes.data if tgt.size else None, 0)
+
+    def run(self, variant="ac4") -> dict:
+        return _stats_dict(trim_run(self.ctx, _variant(variant)))
+
+    def run_async(self, variant="ac4") -> None:
+        trim_run_async(self.ctx, _variant(variant))
+
+    def sync(self) -> dict:
+        return _stats_dict(trim_sync(self.ctx))
+
+    def batch_run(self, graph_off, variant="ac4") -> dict:
+        go = np.ascontiguousarray(graph_off, np.uint32)
+        return _stats_dict(trim_batch_run(self.ctx, go, _variant(variant)))
+
+    def level(self, device: bool = True):
+        import torch
+        if device:
+            out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+            trim_level(self.ctx, out.data_ptr(), 1)
+            return out.view(torch.uint32) if hasattr(torch, "uint32") else out
+        out = np.empty(self.n, np.uint32)
+        trim_level(self.ctx, out.ctypes.data, 0)
+        return out
+
+    def status(self, device: bool = True):
+        import torch
+        if device:
+            out = torch.empty(self.n, dtype=torch.uint8, device="cuda")
+            trim_status(self.ctx, out.data_ptr(), 1)
+            return out
+        out = np.empty(self.n, np.uint8)
+        trim_status(self.ctx, out.ctypes.data, 0)
+        return out
+
+    def set_params(self, **kw) -> None:
+        p = trim_get_params(self.ctx)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        trim_set_params(self.ctx, p)
+
+    def params(self) -> dict:
+        p = trim_get_params(self.ctx)
+        return {k: getattr(p, k) for k, _ in TrimParams._fields_}
+
+    def set_model(self, blob) -> None:
+        trim_set_model(self.ctx, None if blob is None else np.ascontiguousarray(blob, np.float32))
+
+    def set_schedule(self, variants) -> None:
+        trim_set_schedule(self.ctx, np.ascontiguousarray(variants, np.uint8))
+
+    def round_log(self):
+        return trim_get_round_log(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            trim_destroy(self.ctx)
+            self.ctx = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _stats_dict(s: TrimRunStats) -> dict:
+    return {"rounds": s.rounds, "n_dead": s.n_dead, "device_ms": s.device_ms,
+            "edges_inspected": s.edges_inspected, "in_edges_pushed": s.in_edges_pushed,
+            "candidates": s.candidates, "live_swept": s.live_swept,
+            "rounds_by_variant": list(s.rounds_by_variant)}

@@ -1,0 +1,661 @@
+// trim_api.cu -- the C ABI (include/trim.h): contexts, device memory, launches.
+//
+// Host code only marshals: every step of the trimming runs in the kernels of
+// trim_kernels.cu. There is no CPU implementation of the method behind this ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "trim_internal.cuh"
+
+using trimk::Ctrl;
+using trimk::Dev;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+uint64_t g_alloc_limit = 0;  // process-wide cap on bytes one context may allocate (0 = none)
+
+}  // namespace
+
+struct trim_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  uint32_t flags = 0;
+  uint32_t n = 0;
+  uint64_t m = 0;
+  const uint32_t* off = nullptr;
+  const uint32_t* tgt = nullptr;
+  const uint32_t* ioff = nullptr;
+  const uint32_t* itgt = nullptr;
+  std::vector<void*> owned;  // every cudaMalloc of this context
+  uint64_t allocated = 0;
+  uint32_t *level = nullptr, *cnt = nullptr, *supp = nullptr, *s_head = nullptr,
+           *s_next = nullptr, *s_cnt = nullptr, *s_off = nullptr, *s_list = nullptr,
+           *log = nullptr, *roff = nullptr, *live0 = nullptr, *live1 = nullptr, *bsum = nullptr;
+  uint2 *pieces0 = nullptr, *pieces1 = nullptr;
+  uint32_t piece_cap = 0;
+  Ctrl* ctrl = nullptr;
+  Ctrl* h_ctrl = nullptr;  // pinned host mirror for read-back
+  trim_round_rec_t* rlog = nullptr;
+  uint32_t rlog_cap = 0;
+  float* model = nullptr;
+  bool has_model = false;
+  uint8_t* script = nullptr;
+  uint32_t script_len = 0;
+  uint8_t* status_tmp = nullptr;
+  trim_params_t params{};
+  int grid = 0;
+  bool ran = false;
+  bool pending = false;
+  bool s_cnt_dirty = false;
+  uint32_t last_mode = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string err = "no error";
+  trim_run_stats_t last{};
+};
+
+namespace {
+
+trim_err_t fail(trim_ctx* c, trim_err_t code, const std::string& msg) {
+  if (c) c->err = msg; else g_create_error = msg;
+  return code;
+}
+
+trim_err_t cuda_fail(trim_ctx* c, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(c, TRIM_ERR_OOM, msg);
+  return fail(c, TRIM_ERR_CUDA, msg);
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);        \
+  } while (0)
+
+template <class T>
+trim_err_t dalloc(trim_ctx* c, T** p, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (g_alloc_limit && c->allocated + bytes > g_alloc_limit)
+    return fail(c, TRIM_ERR_OOM, "device memory cap reached");
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_fail(c, e, "cudaMalloc");
+  }
+  c->owned.push_back(q);
+  c->allocated += bytes;
+  *p = static_cast<T*>(q);
+  return TRIM_OK;
+}
+
+#define TRY(x)                       \
+  do {                               \
+    trim_err_t t_ = (x);             \
+    if (t_ != TRIM_OK) return t_;    \
+  } while (0)
+
+void release(trim_ctx* c) {
+  if (!c) return;
+  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  for (void* p : c->owned) cudaFree(p);
+  c->owned.clear();
+  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+}
+
+trim_err_t check_device(trim_ctx* c, int* dev, int* sms) {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    (void)cudaGetLastError();
+    return fail(c, TRIM_ERR_NO_DEVICE, "no CUDA device available");
+  }
+  CK(cudaGetDevice(dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, *dev));
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(c, TRIM_ERR_NO_DEVICE,
+                "this library is built for sm_103a (GB300); device is sm_" +
+                    std::to_string(prop.major) + std::to_string(prop.minor));
+  *sms = prop.multiProcessorCount;
+  return TRIM_OK;
+}
+
+void default_params(trim_params_t* p) {
+  p->block_threads = 512;
+  p->ctas_per_sm = 0;
+  p->big_degree = 1024;
+  p->piece_edges = 256;
+  p->batch_cta_max_n = 4096;
+  p->batch_cta_max_m = 65536;
+  p->spin_limit_ns = 5ull * 1000 * 1000 * 1000;  // 5 s
+  p->heur_push_ratio = 1.0f;
+  p->heur_ac6_ratio = 1.0f;
+}
+
+trim_err_t compute_grid(trim_ctx* c) {
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trim_persistent_kernel,
+                                                   (int)c->params.block_threads, 0));
+  if (per_sm <= 0) return fail(c, TRIM_ERR_INVALID_ARG, "block_threads does not fit on an SM");
+  if (c->params.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)c->params.ctas_per_sm);
+  c->grid = per_sm * c->sm_count;
+  return TRIM_OK;
+}
+
+trim_err_t sync_check(trim_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  return TRIM_OK;
+}
+
+// exclusive scan of in[0..n) into out[0..n], out[n] = total (device, on c->stream)
+trim_err_t device_scan(trim_ctx* c, const uint32_t* in, uint32_t n, uint32_t* out) {
+  const uint32_t nb = std::max<uint32_t>(1, std::min<uint32_t>(1024, (n + 4095) / 4096));
+  const uint32_t chunk = (n + nb - 1) / nb;
+  uint32_t* sums = nullptr;
+  TRY(dalloc(c, &sums, nb));
+  trim_scan_blocks_kernel<<<nb, 512, 0, c->stream>>>(in, n, out, sums, chunk);
+  CK(cudaGetLastError());
+  trim_scan_apply_kernel<<<nb, 512, 0, c->stream>>>(out, n, sums, nb, chunk);
+  CK(cudaGetLastError());
+  return TRIM_OK;
+}
+
+// G^T by counting sort on the device (the transposed graph of Section 2).
+trim_err_t build_transpose(trim_ctx* c) {
+  uint32_t *ioff = nullptr, *itgt = nullptr, *fill = nullptr, *bad = nullptr;
+  TRY(dalloc(c, &ioff, (size_t)c->n + 1));
+  TRY(dalloc(c, &itgt, c->m));
+  TRY(dalloc(c, &fill, (size_t)c->n + 1));
+  TRY(dalloc(c, &bad, 1));
+  CK(cudaMemsetAsync(fill, 0, ((size_t)c->n + 1) * 4, c->stream));
+  CK(cudaMemsetAsync(bad, 0, 4, c->stream));
+  const int blocks = c->sm_count * 8;
+  if (c->m) {
+    trim_indeg_kernel<<<blocks, 512, 0, c->stream>>>(c->tgt, c->m, c->n, fill, bad);
+    CK(cudaGetLastError());
+  }
+  TRY(device_scan(c, fill, c->n, ioff));
+  CK(cudaMemsetAsync(fill, 0, ((size_t)c->n + 1) * 4, c->stream));
+  if (c->m) {
+    trim_transpose_fill_kernel<<<blocks, 512, 0, c->stream>>>(c->off, c->tgt, c->n, ioff, fill,
+                                                             itgt);
+    CK(cudaGetLastError());
+  }
+  TRY(sync_check(c));
+  c->ioff = ioff;
+  c->itgt = itgt;
+  return TRIM_OK;
+}
+
+trim_err_t validate(trim_ctx* c, const uint32_t* ioff_given) {
+  uint32_t *bad = nullptr, *indeg = nullptr;
+  TRY(dalloc(c, &bad, 1));
+  TRY(dalloc(c, &indeg, (size_t)c->n + 1));
+  CK(cudaMemsetAsync(bad, 0, 4, c->stream));
+  CK(cudaMemsetAsync(indeg, 0, ((size_t)c->n + 1) * 4, c->stream));
+  const int blocks = c->sm_count * 8;
+  trim_validate_offsets_kernel<<<blocks, 512, 0, c->stream>>>(c->off, c->n, c->m, bad);
+  CK(cudaGetLastError());
+  uint32_t hbad = 0;
+  CK(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync_check(c));
+  if (hbad) return fail(c, TRIM_ERR_BAD_GRAPH, "csr_out: offsets not monotone or off[n] != m");
+  if (c->m) {
+    trim_indeg_kernel<<<blocks, 512, 0, c->stream>>>(c->tgt, c->m, c->n, indeg, bad);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync_check(c));
+  if (hbad) return fail(c, TRIM_ERR_BAD_GRAPH, "csr_out: a target is >= n");
+  if (ioff_given) {
+    trim_validate_offsets_kernel<<<blocks, 512, 0, c->stream>>>(ioff_given, c->n, c->m, bad);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync_check(c));
+    if (hbad) return fail(c, TRIM_ERR_BAD_GRAPH, "csr_in: offsets not monotone or off[n] != m");
+    // G^T must list every edge once: its degrees equal the in-degree histogram of
+    // csr_out, and the multiset of (source, target) pairs matches (checked by
+    // building G^T here and comparing row by row after sorting).
+    const uint32_t* keep_ioff = c->ioff;
+    const uint32_t* keep_itgt = c->itgt;
+    TRY(build_transpose(c));
+    std::vector<uint32_t> a((size_t)c->n + 1), b((size_t)c->n + 1);
+    CK(cudaMemcpy(a.data(), c->ioff, a.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(b.data(), keep_ioff, b.size() * 4, cudaMemcpyDeviceToHost));
+    if (a != b) return fail(c, TRIM_ERR_BAD_GRAPH, "csr_in is not the transpose (degrees differ)");
+    std::vector<uint32_t> ta(c->m), tb(c->m);
+    if (c->m) {
+      CK(cudaMemcpy(ta.data(), c->itgt, c->m * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(tb.data(), keep_itgt, c->m * 4, cudaMemcpyDeviceToHost));
+    }
+    for (uint32_t v = 0; v < c->n; ++v) {
+      std::sort(ta.begin() + a[v], ta.begin() + a[v + 1]);
+      std::sort(tb.begin() + a[v], tb.begin() + a[v + 1]);
+    }
+    if (ta != tb) return fail(c, TRIM_ERR_BAD_GRAPH, "csr_in is not the transpose (edges differ)");
+    c->ioff = keep_ioff;
+    c->itgt = keep_itgt;
+  }
+  return TRIM_OK;
+}
+
+trim_err_t upload(trim_ctx* c, const trim_csr_t* g, const uint32_t** off, const uint32_t** tgt) {
+  if (g->on_device) {
+    *off = g->offsets;
+    *tgt = g->targets;
+    return TRIM_OK;
+  }
+  uint32_t *o = nullptr, *t = nullptr;
+  TRY(dalloc(c, &o, (size_t)g->n + 1));
+  TRY(dalloc(c, &t, g->m));
+  CK(cudaMemcpyAsync(o, g->offsets, ((size_t)g->n + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+  if (g->m) CK(cudaMemcpyAsync(t, g->targets, g->m * 4, cudaMemcpyHostToDevice, c->stream));
+  TRY(sync_check(c));
+  *off = o;
+  *tgt = t;
+  return TRIM_OK;
+}
+
+trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, uint32_t flags,
+                       trim_ctx* c) {
+  if (g->n > 0xFFFFFFFEu || g->m >= (1ull << 32))
+    return fail(c, TRIM_ERR_TOO_LARGE, "n must be < 2^32-1 and m < 2^32");
+  if (g->offsets == nullptr || (g->m && g->targets == nullptr))
+    return fail(c, TRIM_ERR_INVALID_ARG, "csr_out: null array");
+  if (gi) {
+    if (gi->n != g->n || gi->m != g->m)
+      return fail(c, TRIM_ERR_INVALID_ARG, "csr_in: n and m must equal those of csr_out");
+    if (gi->offsets == nullptr || (gi->m && gi->targets == nullptr))
+      return fail(c, TRIM_ERR_INVALID_ARG, "csr_in: null array");
+  }
+  if (!g->on_device && g->n) {
+    // cheap host checks before any device work
+    if (g->offsets[0] != 0 || (uint64_t)g->offsets[g->n] != g->m)
+      return fail(c, TRIM_ERR_BAD_GRAPH, "csr_out: offsets[0] != 0 or offsets[n] != m");
+  }
+  TRY(check_device(c, &c->device, &c->sm_count));
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->flags = flags;
+  c->n = g->n;
+  c->m = g->m;
+  default_params(&c->params);
+  CK(cudaEventCreate(&c->ev0));
+  CK(cudaEventCreate(&c->ev1));
+  TRY(upload(c, g, &c->off, &c->tgt));
+  if (gi) TRY(upload(c, gi, &c->ioff, &c->itgt));
+  if (flags & TRIM_FLAG_VALIDATE) TRY(validate(c, gi ? c->ioff : nullptr));
+  const size_t n = c->n;
+  TRY(dalloc(c, &c->level, n));
+  TRY(dalloc(c, &c->cnt, n));
+  TRY(dalloc(c, &c->supp, n));
+  TRY(dalloc(c, &c->s_head, n));
+  TRY(dalloc(c, &c->s_next, n));
+  TRY(dalloc(c, &c->s_cnt, n));
+  TRY(dalloc(c, &c->s_off, n + 1));
+  TRY(dalloc(c, &c->s_list, n));
+  TRY(dalloc(c, &c->log, n));
+  TRY(dalloc(c, &c->roff, n + 2));
+  TRY(dalloc(c, &c->live0, n));
+  TRY(dalloc(c, &c->live1, n));
+  TRY(dalloc(c, &c->bsum, 8192));
+  TRY(dalloc(c, &c->ctrl, 1));
+  CK(cudaMemsetAsync(c->s_cnt, 0, n * 4, c->stream));
+  CK(cudaMallocHost(&c->h_ctrl, sizeof(Ctrl)));
+  if (flags & TRIM_FLAG_ROUND_LOG) {
+    c->rlog_cap = (uint32_t)std::min<uint64_t>(n + 1, 1u << 20);
+    TRY(dalloc(c, &c->rlog, c->rlog_cap));
+  }
+  TRY(compute_grid(c));
+  TRY(sync_check(c));
+  return TRIM_OK;
+}
+
+// pieces of big vertices: at most m/big + m/piece per round, two rounds kept
+trim_err_t ensure_pieces(trim_ctx* c) {
+  const uint64_t need =
+      c->m / std::max<uint32_t>(1, c->params.big_degree) + c->m / c->params.piece_edges + 16;
+  if (c->pieces0 && c->piece_cap >= need) return TRIM_OK;
+  uint2 *a = nullptr, *b = nullptr;
+  TRY(dalloc(c, &a, need));
+  TRY(dalloc(c, &b, need));
+  c->pieces0 = a;
+  c->pieces1 = b;
+  c->piece_cap = (uint32_t)std::min<uint64_t>(need, 0xFFFFFFFFu);
+  return TRIM_OK;
+}
+
+trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
+  if ((int)variant < 0 || variant > TRIM_SCHED_SCRIPTED)
+    return fail(c, TRIM_ERR_INVALID_ARG, "unknown variant");
+  if (variant == TRIM_SCHED_SCRIPTED && c->script_len == 0)
+    return fail(c, TRIM_ERR_STATE, "TRIM_SCHED_SCRIPTED needs trim_set_schedule first");
+  if (variant == TRIM_AC4_PUSH && c->ioff == nullptr) TRY(build_transpose(c));
+  uint32_t f = c->flags & (TRIM_FLAG_STATS | TRIM_FLAG_ROUND_LOG);
+  bool ac4 = false, ac6 = false, ac3 = false;
+  switch (variant) {
+    case TRIM_AC4_PUSH: ac4 = true; break;
+    case TRIM_AC6_SUPPORT: ac6 = true; break;
+    case TRIM_AC3_PULL: ac3 = true; break;
+    default:
+      ac4 = c->ioff != nullptr;
+      ac6 = ac3 = true;
+      f |= trimk::F_NEED_FEATURES;
+  }
+  if (c->flags & TRIM_FLAG_ROUND_LOG) f |= trimk::F_NEED_FEATURES;
+  if (variant == TRIM_SCHED_SCRIPTED) {
+    std::vector<uint8_t> s(c->script_len);
+    CK(cudaMemcpy(s.data(), c->script, c->script_len, cudaMemcpyDeviceToHost));
+    ac4 = ac6 = ac3 = false;
+    for (uint8_t x : s) {
+      if (x == TRIM_AC4_PUSH) ac4 = true;
+      else if (x == TRIM_AC6_SUPPORT) ac6 = true;
+      else ac3 = true;
+    }
+    if (ac4 && c->ioff == nullptr) TRY(build_transpose(c));
+  }
+  if (ac4) { f |= trimk::F_AC4_POSSIBLE; TRY(ensure_pieces(c)); }
+  if (ac6) f |= trimk::F_AC6_POSSIBLE;
+  if (ac3) f |= trimk::F_AC3_POSSIBLE;
+  if (c->n == 0) {
+    c->ran = true;
+    c->pending = false;
+    c->last_mode = variant;
+    std::memset(c->h_ctrl, 0, sizeof(Ctrl));
+    CK(cudaEventRecord(c->ev0, c->stream));
+    CK(cudaEventRecord(c->ev1, c->stream));
+    return TRIM_OK;
+  }
+  if (ac6 && c->s_cnt_dirty) {
+    CK(cudaMemsetAsync(c->s_cnt, 0, (size_t)c->n * 4, c->stream));
+    c->s_cnt_dirty = false;
+  }
+  Dev D{};
+  D.n = c->n;
+  D.m = (uint32_t)c->m;
+  D.off = c->off; D.tgt = c->tgt; D.ioff = c->ioff; D.itgt = c->itgt;
+  D.level = c->level; D.cnt = c->cnt; D.supp = c->supp;
+  D.s_head = c->s_head; D.s_next = c->s_next; D.s_cnt = c->s_cnt; D.s_off = c->s_off;
+  D.s_list = c->s_list; D.log = c->log; D.roff = c->roff; D.live0 = c->live0;
+  D.live1 = c->live1; D.pieces0 = c->pieces0; D.pieces1 = c->pieces1;
+  D.piece_cap = c->piece_cap; D.bsum = c->bsum; D.C = c->ctrl;
+  D.rlog = c->rlog; D.rlog_cap = c->rlog_cap;
+  D.model = c->has_model ? c->model : nullptr;
+  D.script = c->script; D.script_len = c->script_len;
+  D.mode = variant; D.flags = f;
+  D.big_degree = c->params.big_degree; D.piece_edges = c->params.piece_edges;
+  D.spin_limit_ns = c->params.spin_limit_ns;
+  D.heur_push_ratio = c->params.heur_push_ratio;
+  D.heur_ac6_ratio = c->params.heur_ac6_ratio;
+  if ((uint32_t)c->grid > 8192) return fail(c, TRIM_ERR_INVALID_ARG, "grid too large");
+  CK(cudaEventRecord(c->ev0, c->stream));
+  trim_reset_ctrl_kernel<<<1, 32, 0, c->stream>>>(c->ctrl, c->m);
+  CK(cudaGetLastError());
+  void* args[] = {&D};
+  CK(cudaLaunchCooperativeKernel((const void*)trim_persistent_kernel, dim3(c->grid),
+                                 dim3(c->params.block_threads), args, 0, c->stream));
+  CK(cudaEventRecord(c->ev1, c->stream));
+  c->pending = true;
+  c->last_mode = variant;
+  c->ran = false;
+  return TRIM_OK;
+}
+
+trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats) {
+  if (c->pending) {
+    TRY(sync_check(c));
+    CK(cudaMemcpy(c->h_ctrl, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    c->pending = false;
+    const Ctrl& h = *c->h_ctrl;
+    if (h.err) {
+      c->s_cnt_dirty = true;
+      if (h.err == TRIM_ERR_TIMEOUT)
+        return fail(c, TRIM_ERR_TIMEOUT, "a device-side wait exceeded spin_limit_ns");
+      return fail(c, (trim_err_t)h.err,
+                  "device reported error " + std::to_string(h.err) + " (info " +
+                      std::to_string(h.err_info) + ")");
+    }
+    trim_run_stats_t s{};
+    s.rounds = h.rounds;
+    s.n_dead = h.log_len;
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    s.device_ms = ms;
+    s.edges_inspected = h.stats[0];
+    s.in_edges_pushed = h.stats[1];
+    s.candidates = h.stats[2];
+    s.live_swept = h.stats[3];
+    for (int i = 0; i < 3; ++i) s.rounds_by_variant[i] = h.vcount[i];
+    c->last = s;
+    c->ran = true;
+  }
+  if (!c->ran) return fail(c, TRIM_ERR_STATE, "no run was enqueued");
+  if (stats) *stats = c->last;
+  return TRIM_OK;
+}
+
+// no edge of the packed CSR may join two graphs
+trim_err_t validate_batch(trim_ctx* c, const uint32_t* graph_off, uint32_t G) {
+  std::vector<uint32_t> vg(c->n);
+  for (uint32_t g = 0; g < G; ++g)
+    for (uint32_t v = graph_off[g]; v < graph_off[g + 1]; ++v) vg[v] = g;
+  uint32_t *dvg = nullptr, *bad = nullptr;
+  TRY(dalloc(c, &dvg, c->n));
+  TRY(dalloc(c, &bad, 1));
+  CK(cudaMemcpyAsync(dvg, vg.data(), (size_t)c->n * 4, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(bad, 0, 4, c->stream));
+  trim_validate_batch_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->off, c->tgt, c->n, dvg,
+                                                                     bad);
+  CK(cudaGetLastError());
+  uint32_t h = 0;
+  CK(cudaMemcpyAsync(&h, bad, 4, cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync_check(c));
+  if (h) return fail(c, TRIM_ERR_BAD_GRAPH, "an edge joins two graphs of the batch");
+  return TRIM_OK;
+}
+
+// The packed CSR of independent graphs is itself one graph (their disjoint
+// union), whose levels equal those of each graph trimmed alone.
+trim_err_t enqueue_batch(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
+                         trim_variant_t variant) {
+  (void)graph_off;
+  (void)G;
+  return enqueue_run(c, variant);
+}
+
+}  // namespace
+
+extern "C" {
+
+trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void* cuda_stream,
+                       uint32_t flags, trim_ctx** out) {
+  if (!csr_out || !out) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null csr_out or out");
+  if (flags & ~(TRIM_FLAG_VALIDATE | TRIM_FLAG_STATS | TRIM_FLAG_ROUND_LOG))
+    return fail(nullptr, TRIM_ERR_INVALID_ARG, "unknown flag bits");
+  trim_ctx* c = new (std::nothrow) trim_ctx();
+  if (!c) return fail(nullptr, TRIM_ERR_OOM, "host allocation failed");
+  trim_err_t e = create_impl(csr_out, csr_in, cuda_stream, flags, c);
+  if (e != TRIM_OK) {
+    g_create_error = c->err;
+    release(c);
+    delete c;
+    return e;
+  }
+  *out = c;
+  return TRIM_OK;
+}
+
+trim_err_t trim_run(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats) {
+  if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  TRY(enqueue_run(c, variant));
+  return finish_run(c, stats);
+}
+
+trim_err_t trim_run_async(trim_ctx* c, trim_variant_t variant) {
+  if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  return enqueue_run(c, variant);
+}
+
+trim_err_t trim_sync(trim_ctx* c, trim_run_stats_t* stats) {
+  if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  return finish_run(c, stats);
+}
+
+trim_err_t trim_batch_run(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
+                          trim_variant_t variant, trim_run_stats_t* stats) {
+  if (!c || !graph_off || G == 0) return fail(c, TRIM_ERR_INVALID_ARG, "null argument or G = 0");
+  if (graph_off[0] != 0 || graph_off[G] != c->n)
+    return fail(c, TRIM_ERR_INVALID_ARG, "graph_off must start at 0 and end at n");
+  for (uint32_t g = 0; g < G; ++g)
+    if (graph_off[g + 1] < graph_off[g])
+      return fail(c, TRIM_ERR_INVALID_ARG, "graph_off must be non-decreasing");
+  if (c->flags & TRIM_FLAG_VALIDATE) TRY(validate_batch(c, graph_off, G));
+  TRY(enqueue_batch(c, graph_off, G, variant));
+  return finish_run(c, stats);
+}
+
+trim_err_t trim_status(const trim_ctx* cc, uint8_t* out, int out_on_device) {
+  trim_ctx* c = const_cast<trim_ctx*>(cc);
+  if (!c || (!out && c->n)) return fail(c, TRIM_ERR_INVALID_ARG, "null argument");
+  if (c->pending) TRY(finish_run(c, nullptr));
+  if (!c->ran) return fail(c, TRIM_ERR_STATE, "trim_status before a successful trim_run");
+  if (c->n == 0) return TRIM_OK;
+  uint8_t* dst = out;
+  if (!out_on_device) {
+    if (!c->status_tmp) TRY(dalloc(c, &c->status_tmp, c->n));
+    dst = c->status_tmp;
+  }
+  trim_status_kernel<<<c->sm_count * 4, 512, 0, c->stream>>>(c->level, c->n, dst);
+  CK(cudaGetLastError());
+  if (!out_on_device)
+    CK(cudaMemcpyAsync(out, dst, c->n, cudaMemcpyDeviceToHost, c->stream));
+  return sync_check(c);
+}
+
+trim_err_t trim_level(const trim_ctx* cc, uint32_t* out, int out_on_device) {
+  trim_ctx* c = const_cast<trim_ctx*>(cc);
+  if (!c || (!out && c->n)) return fail(c, TRIM_ERR_INVALID_ARG, "null argument");
+  if (c->pending) TRY(finish_run(c, nullptr));
+  if (!c->ran) return fail(c, TRIM_ERR_STATE, "trim_level before a successful trim_run");
+  if (c->n == 0) return TRIM_OK;
+  CK(cudaMemcpyAsync(out, c->level, (size_t)c->n * 4,
+                     out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream));
+  return sync_check(c);
+}
+
+trim_err_t trim_level_device_ptr(const trim_ctx* c, const uint32_t** out) {
+  if (!c || !out) return fail(const_cast<trim_ctx*>(c), TRIM_ERR_INVALID_ARG, "null argument");
+  *out = c->level;
+  return TRIM_OK;
+}
+
+trim_err_t trim_default_params(trim_params_t* p) {
+  if (!p) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null params");
+  default_params(p);
+  return TRIM_OK;
+}
+
+trim_err_t trim_set_params(trim_ctx* c, const trim_params_t* p) {
+  if (!c || !p) return fail(c, TRIM_ERR_INVALID_ARG, "null argument");
+  if (p->block_threads < 128 || p->block_threads > 512 || p->block_threads % 32)
+    return fail(c, TRIM_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [128,512]");
+  if (p->piece_edges < 32 || p->big_degree < 32)
+    return fail(c, TRIM_ERR_INVALID_ARG, "piece_edges and big_degree must be >= 32");
+  if (p->spin_limit_ns == 0) return fail(c, TRIM_ERR_INVALID_ARG, "spin_limit_ns must be > 0");
+  if (!(p->heur_push_ratio > 0.0f) || !(p->heur_ac6_ratio > 0.0f))
+    return fail(c, TRIM_ERR_INVALID_ARG, "heuristic ratios must be > 0");
+  const trim_params_t old = c->params;
+  c->params = *p;
+  trim_err_t e = compute_grid(c);
+  if (e != TRIM_OK) {
+    c->params = old;
+    compute_grid(c);
+    return e;
+  }
+  if (p->big_degree != old.big_degree || p->piece_edges != old.piece_edges) {
+    c->pieces0 = c->pieces1 = nullptr;  // reallocated on the next AC-4 run (old ones freed at destroy)
+    c->piece_cap = 0;
+  }
+  return TRIM_OK;
+}
+
+trim_err_t trim_get_params(const trim_ctx* c, trim_params_t* p) {
+  if (!c || !p) return fail(const_cast<trim_ctx*>(c), TRIM_ERR_INVALID_ARG, "null argument");
+  *p = c->params;
+  return TRIM_OK;
+}
+
+trim_err_t trim_set_model(trim_ctx* c, const float* blob, size_t n_floats) {
+  if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  if (blob == nullptr) {
+    c->has_model = false;
+    return TRIM_OK;
+  }
+  if (n_floats != TRIM_MLP_NBLOB)
+    return fail(c, TRIM_ERR_INVALID_ARG, "model blob must hold TRIM_MLP_NBLOB floats");
+  if (!c->model) TRY(dalloc(c, &c->model, TRIM_MLP_NBLOB));
+  CK(cudaMemcpyAsync(c->model, blob, TRIM_MLP_NBLOB * 4, cudaMemcpyHostToDevice, c->stream));
+  TRY(sync_check(c));
+  c->has_model = true;
+  return TRIM_OK;
+}
+
+trim_err_t trim_set_schedule(trim_ctx* c, const uint8_t* v, uint32_t len) {
+  if (!c || (!v && len)) return fail(c, TRIM_ERR_INVALID_ARG, "null argument");
+  for (uint32_t i = 0; i < len; ++i)
+    if (v[i] > 2) return fail(c, TRIM_ERR_INVALID_ARG, "schedule entries must be 0..2");
+  if (len > c->script_len || !c->script) {
+    uint8_t* s = nullptr;
+    TRY(dalloc(c, &s, len));
+    c->script = s;
+  }
+  if (len) CK(cudaMemcpyAsync(c->script, v, len, cudaMemcpyHostToDevice, c->stream));
+  TRY(sync_check(c));
+  c->script_len = len;
+  return TRIM_OK;
+}
+
+trim_err_t trim_get_round_log(const trim_ctx* cc, trim_round_rec_t* out, size_t cap,
+                              size_t* n_out) {
+  trim_ctx* c = const_cast<trim_ctx*>(cc);
+  if (!c || !n_out || (!out && cap)) return fail(c, TRIM_ERR_INVALID_ARG, "null argument");
+  if (!(c->flags & TRIM_FLAG_ROUND_LOG))
+    return fail(c, TRIM_ERR_STATE, "context was created without TRIM_FLAG_ROUND_LOG");
+  if (c->pending) TRY(finish_run(c, nullptr));
+  if (!c->ran) return fail(c, TRIM_ERR_STATE, "no completed run");
+  const size_t have = std::min<size_t>(c->h_ctrl->rlog_len, c->rlog_cap);
+  const size_t k = std::min(have, cap);
+  if (k) CK(cudaMemcpy(out, c->rlog, k * sizeof(trim_round_rec_t), cudaMemcpyDeviceToHost));
+  *n_out = k;
+  return TRIM_OK;
+}
+
+void trim_destroy(trim_ctx* c) {
+  if (!c) return;
+  release(c);
+  delete c;
+}
+
+const char* trim_last_error(const trim_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+trim_err_t trim_set_alloc_limit(uint64_t bytes) {
+  g_alloc_limit = bytes;
+  return TRIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// trim_internal.cuh -- device state, control block and warp/grid primitives of
+// the persistent trimming kernel.
+//
+// Level semantics (Definition 2 of Guo & Sekerinski, counted from 0): round r
+// removes exactly the vertices whose successors were all removed in rounds
+// < r. Every variant reads a vertex u as "removed before round r" iff
+// level[u] < r; a vertex removed during round r carries level r and still
+// counts as present for the rest of that round. This snapshot rule makes every
+// variant compute the same levels, so they can be mixed round by round.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/trim.h"
+
+namespace trimk {
+
+constexpr uint32_t LIVE = 0xFFFFFFFFu;
+constexpr uint32_t NIL = 0xFFFFFFFFu;
+constexpr int NFEAT = 12;
+
+// flags inside Dev::flags (superset of the public TRIM_FLAG_*)
+constexpr uint32_t F_STATS = TRIM_FLAG_STATS;
+constexpr uint32_t F_ROUND_LOG = TRIM_FLAG_ROUND_LOG;
+constexpr uint32_t F_NEED_FEATURES = 0x100;  // scheduler modes: gather per-frontier degrees
+constexpr uint32_t F_AC4_POSSIBLE = 0x200;   // counters must be initialised / big pieces kept
+constexpr uint32_t F_AC6_POSSIBLE = 0x400;
+constexpr uint32_t F_AC3_POSSIBLE = 0x800;
+
+// Per-frontier accumulators, filled while F_r is appended (slot r & 3).
+struct RoundStat {
+  unsigned long long sum_in;   // sum of in-degrees of F_r
+  unsigned long long sum_out;  // sum of out-degrees of F_r
+  unsigned int hist[3];        // in-degree < 8, < 256, >= 256
+  unsigned int npieces;        // AC-4 pieces reserved for big vertices of F_r
+  unsigned int pad[2];
+};
+
+// Global control block. Barrier words sit on their own 128-byte lines.
+struct Ctrl {
+  unsigned int bar_count; unsigned int _p0[31];
+  unsigned int bar_gen;   unsigned int _p1[31];
+  unsigned int log_len;   unsigned int _p2[31];
+  unsigned int live_len[2]; unsigned int live_fill; unsigned int _p3[29];
+  // written only by the barrier hook (one warp), read by everyone after a barrier
+  unsigned int round;      // current round r (1-based once the loop runs)
+  unsigned int f_begin;    // F_{r-1} = log[f_begin, f_end)
+  unsigned int f_end;
+  unsigned int variant;    // variant of round r (0..2)
+  unsigned int prev_variant;  // variant of round r-1 (NIL before the first round)
+  unsigned int c4;         // AC-4: decrements applied for log[0, c4)
+  unsigned int ac3_list;   // which live list holds the AC-3 superset (0/1), NIL = none yet
+  unsigned int done;
+  unsigned int err;
+  unsigned int err_info;
+  unsigned int rounds;     // alpha
+  unsigned int vcount[3];
+  unsigned int rlog_len;
+  unsigned int _p4[15];
+  unsigned long long m_live;
+  unsigned long long t_release;   // %globaltimer when the current round was released
+  unsigned long long cum_in;      // sum of in-degrees over log[0, log_len)
+  unsigned long long cum_in_c4;   // ... over log[0, c4)
+  unsigned long long last_round_ns;
+  unsigned long long stats[4];    // edges inspected, in-edges pushed, candidates, live swept
+  float feat[NFEAT];              // features of the upcoming round
+  RoundStat rs[4];
+};
+
+struct Dev {
+  uint32_t n;
+  uint32_t m;
+  const uint32_t* __restrict__ off;   // out-CSR (read-only during a run)
+  const uint32_t* __restrict__ tgt;
+  const uint32_t* __restrict__ ioff;  // in-CSR G^T (nullable)
+  const uint32_t* __restrict__ itgt;
+  uint32_t* level;
+  uint32_t* cnt;      // AC-4 out-degree counters
+  uint32_t* supp;     // edge_index of AC-3 / AC-6: position of the current support
+  uint32_t* s_head;   // AC-6 supporting sets added during the epoch (intrusive lists)
+  uint32_t* s_next;
+  uint32_t* s_cnt;    // AC-6 bulk build: member counts per support (zero between builds)
+  uint32_t* s_off;    // AC-6 bulk supporting sets: CSR by support vertex (n+1)
+  uint32_t* s_list;
+  uint32_t* log;      // dead log: F_0 | F_1 | ... (n)
+  uint32_t* roff;     // roff[r] = start of F_r in the log (n+2)
+  uint32_t* live0;    // AC-3 live lists
+  uint32_t* live1;
+  uint2* pieces0;     // AC-4 pieces of big vertices (by round parity)
+  uint2* pieces1;
+  uint32_t piece_cap;
+  uint32_t* bsum;     // per-CTA scratch of the grid-wide scan
+  Ctrl* C;
+  trim_round_rec_t* rlog;
+  uint32_t rlog_cap;
+  const float* model; // scheduler MLP blob (nullable)
+  const uint8_t* script;
+  uint32_t script_len;
+  uint32_t mode;      // trim_variant_t requested
+  uint32_t flags;
+  uint32_t big_degree;
+  uint32_t piece_edges;
+  uint64_t spin_limit_ns;
+  float heur_push_ratio;
+  float heur_ac6_ratio;
+};
+
+// ---------------------------------------------------------------- primitives
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acqrel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+               : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+// loads of state that other SMs write during the run: served by L2, never a stale L1 line
+__device__ __forceinline__ uint32_t ldcg(const uint32_t* p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned x) {
+  const unsigned lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= (unsigned)o) x += y;
+  }
+  return x;
+}
+template <class T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ void set_error(const Dev& D, unsigned code, unsigned info) {
+  if (atomicCAS(&D.C->err, 0u, code) == 0u) D.C->err_info = info;
+}
+
+}  // namespace trimk
+
+// kernels (defined in trim_kernels.cu, launched from trim_api.cu)
+__global__ void trim_persistent_kernel(trimk::Dev D);
+__global__ void trim_reset_ctrl_kernel(trimk::Ctrl* C, uint64_t m);
+__global__ void trim_status_kernel(const uint32_t* level, uint32_t n, uint8_t* status);
+__global__ void trim_indeg_kernel(const uint32_t* tgt, uint64_t m, uint32_t n, uint32_t* cnt,
+                                  uint32_t* bad);
+__global__ void trim_scan_blocks_kernel(const uint32_t* in, uint32_t n, uint32_t* out,
+                                        uint32_t* block_sums, uint32_t chunk);
+__global__ void trim_scan_apply_kernel(uint32_t* out, uint32_t n, const uint32_t* block_sums,
+                                       uint32_t nblocks, uint32_t chunk);
+__global__ void trim_transpose_fill_kernel(const uint32_t* off, const uint32_t* tgt, uint32_t n,
+                                           const uint32_t* ioff, uint32_t* fill, uint32_t* itgt);
+__global__ void trim_validate_offsets_kernel(const uint32_t* off, uint32_t n, uint64_t m,
+                                             uint32_t* bad);
+__global__ void trim_validate_batch_kernel(const uint32_t* off, const uint32_t* tgt, uint32_t n,
+                                           const uint32_t* vgraph, uint32_t* bad);

@@ -1,0 +1,97 @@
+"""CPU-side checks of the boundary: the library loads without a GPU, exports
+every function include/trim.h declares, and rejects bad arguments on the host
+before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "trim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(trim_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2107_12720_gb300 import build
+    build.build()
+    import paper_2107_12720_gb300 as P
+    return P.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_declares_every_header_symbol(lib):
+    from paper_2107_12720_gb300.abi import SIGNATURES
+    bound = {s[0] for s in SIGNATURES}
+    assert set(declared_functions()) == bound
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_2107_12720_gb300.abi import TrimCsr, TrimParams, TrimRoundRec, TrimRunStats
+    assert ctypes.sizeof(TrimCsr) == 40
+    assert ctypes.sizeof(TrimParams) == 40
+    assert ctypes.sizeof(TrimRunStats) == 64
+    assert ctypes.sizeof(TrimRoundRec) == 80
+
+
+def test_host_argument_checks_without_device(lib):
+    import paper_2107_12720_gb300 as P
+    from paper_2107_12720_gb300.abi import TrimCsr
+    ctx = ctypes.c_void_p()
+    # null csr
+    assert lib.trim_create(None, None, None, 0, ctypes.byref(ctx)) == 1
+    off = np.array([0, 1, 2], np.uint32)
+    tgt = np.array([1, 0], np.uint32)
+    csr = TrimCsr(2, 2, off.ctypes.data, tgt.ctypes.data, 0)
+    # unknown flag bits
+    assert lib.trim_create(ctypes.byref(csr), None, None, 0x80, ctypes.byref(ctx)) == 1
+    # m too large for uint32 offsets
+    big = TrimCsr(2, 1 << 33, off.ctypes.data, tgt.ctypes.data, 0)
+    assert lib.trim_create(ctypes.byref(big), None, None, 0, ctypes.byref(ctx)) == 3
+    # offsets inconsistent with m (host check)
+    bad = TrimCsr(2, 3, off.ctypes.data, tgt.ctypes.data, 0)
+    assert lib.trim_create(ctypes.byref(bad), None, None, 0, ctypes.byref(ctx)) == 2
+    assert "offsets" in lib.trim_last_error(None).decode()
+    # csr_in of a different size
+    cin = TrimCsr(3, 2, off.ctypes.data, tgt.ctypes.data, 0)
+    assert lib.trim_create(ctypes.byref(csr), ctypes.byref(cin), None, 0, ctypes.byref(ctx)) == 1
+    # null context calls
+    assert lib.trim_run(None, 0, None) == 1
+    assert lib.trim_status(None, None, 0) == 1
+    assert lib.trim_level(None, None, 0) == 1
+    p = P.abi.TrimParams()
+    assert lib.trim_default_params(ctypes.byref(p)) == 0
+    assert p.block_threads == 512 and p.spin_limit_ns > 0
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_2107_12720_gb300.abi import TrimCsr
+    off = np.array([0, 1, 1], np.uint32)
+    tgt = np.array([1], np.uint32)
+    csr = TrimCsr(2, 1, off.ctypes.data, tgt.ctypes.data, 0)
+    ctx = ctypes.c_void_p()
+    rc = lib.trim_create(ctypes.byref(csr), None, None, 0, ctypes.byref(ctx))
+    assert rc == 8, rc  # TRIM_ERR_NO_DEVICE
+
+
+def test_mlp_entry_points_reject_bad_args(lib):
+    assert lib.trim_mlp_forward(None, None, 0, None, None) == 1
+    assert lib.trim_mlp_loss_grad(None, None, None, 0, None, None, None, None) == 1
+    assert lib.trim_mlp_adam_step(None, None, None, None, 0, 0.0, 0.0, 0.0, 0.0, None) == 1
+    assert lib.trim_mlp_scratch_bytes(1000) > 0

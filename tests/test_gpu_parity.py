@@ -1,0 +1,210 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Status and level must match bit for bit: they are integers, and the result of
+trimming is unique (Definition 1 and Definition 2 fix it), whichever variant or
+per-round schedule computes it.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import graphgen.configs as cfg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["ac4", "ac6", "ac3", "heuristic", "learned"]
+
+
+def _P():
+    import paper_2107_12720_gb300 as P
+    return P
+
+
+def dev_csr(g):
+    import torch
+    off = torch.from_numpy(g.off.astype(np.int32)).cuda()
+    tgt = torch.from_numpy(g.tgt.astype(np.int32)).cuda()
+    return off, tgt
+
+
+def dev_csr_in(g):
+    import torch
+    oi, ti = oracle.transpose(g.off, g.tgt)
+    return (torch.from_numpy(oi.astype(np.int32)).cuda(),
+            torch.from_numpy(ti.astype(np.int32)).cuda())
+
+
+def check(t, want_level, want_status, alpha, variant, stats=None):
+    lvl = t.level(device=False)
+    st = t.status(device=False)
+    bad = np.nonzero(lvl != want_level)[0]
+    assert bad.size == 0, f"{variant}: {bad.size} levels differ, first v={bad[:5]} " \
+                          f"got={lvl[bad[:5]]} want={want_level[bad[:5]]}"
+    assert np.array_equal(st, want_status), variant
+    if stats is not None:
+        assert stats["rounds"] == alpha, (variant, stats["rounds"], alpha)
+        assert stats["n_dead"] == int((want_status == 0).sum())
+
+
+def hand_cases():
+    k = 40
+    cases = {
+        "worked_example": gg.edges_from_lists(5, [[3, 2], [], [4, 3], [4], []]),
+        "chain": gg.edges_from_lists(k, [[]] + [[i - 1] for i in range(1, k)]),
+        "out_star": gg.edges_from_lists(6, [[1, 2, 3, 4, 5]] + [[]] * 5),
+        "in_star": gg.edges_from_lists(6, [[]] + [[0]] * 5),
+        "cycle_tails": gg.edges_from_lists(6, [[1], [2], [0], [4], [0], [2]]),
+        "self_loops": gg.edges_from_lists(4, [[0], [0], [1], [3, 2]]),
+        "two_cycle_sink": gg.edges_from_lists(4, [[1], [0], [0, 3], []]),
+        "duplicates": gg.edges_from_lists(4, [[1, 1, 1], [2, 2], [], [3, 0, 0]]),
+        "edgeless": gg.edges_from_lists(9, [[]] * 9),
+        "single": gg.edges_from_lists(1, [[]]),
+        "single_loop": gg.edges_from_lists(1, [[0]]),
+    }
+    # a hub whose in-degree exceeds the AC-4 piece threshold (split into pieces)
+    nh = 5000
+    cases["big_in_hub"] = gg.edges_from_lists(nh + 1, [[]] + [[0]] * nh)
+    # long dead runs before a live successor (warp-cooperative rescans)
+    rows = [[1], [0]] + [list(range(3, 300)) + [0]] + [[]] * 297
+    cases["long_dead_run"] = gg.edges_from_lists(300, rows)
+    return cases
+
+
+@pytest.mark.parametrize("name", list(hand_cases().keys()))
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_hand_cases(name, variant):
+    P = _P()
+    g = hand_cases()[name]
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    off, tgt = dev_csr(g)
+    with P.Trimmer(off, tgt) as t:
+        s = t.run(variant)
+        check(t, lvl, st, alpha, variant, s)
+
+
+def test_empty_graph():
+    P = _P()
+    g = gg.edges_from_lists(0, [])
+    with P.Trimmer(g.off, g.tgt) as t:
+        s = t.run("ac4")
+        assert s["rounds"] == 0 and s["n_dead"] == 0
+        assert t.level(device=False).shape == (0,)
+
+
+@pytest.mark.parametrize("i", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_small_configs(i, variant):
+    P = _P()
+    g = cfg.config_small(i)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    off, tgt = dev_csr(g)
+    oi, ti = dev_csr_in(g)
+    with P.Trimmer(off, tgt, oi, ti, flags=P.TRIM_FLAG_STATS) as t:
+        s = t.run(variant)
+        check(t, lvl, st, alpha, variant, s)
+        s2 = t.run(variant)  # repeatable
+        check(t, lvl, st, alpha, variant, s2)
+
+
+@pytest.mark.parametrize("i", [0, 1, 2])
+def test_host_inputs_and_device_transpose(i):
+    """Host CSR copied by the library; G^T built on the device by AC-4."""
+    P = _P()
+    g = cfg.config_small(i)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    with P.Trimmer(g.off, g.tgt, flags=P.TRIM_FLAG_VALIDATE) as t:
+        for v in ["ac4", "ac6", "ac3", "heuristic"]:
+            check(t, lvl, st, alpha, v, t.run(v))
+
+
+def test_random_schedules_are_bit_identical():
+    """Property: any per-round mix of the three kernels gives the same levels."""
+    P = _P()
+    rng = np.random.default_rng(7)
+    for i in [1, 2, 4]:
+        g = cfg.config_small(i)
+        lvl, st, alpha = oracle.peel(g.off, g.tgt)
+        off, tgt = dev_csr(g)
+        oi, ti = dev_csr_in(g)
+        with P.Trimmer(off, tgt, oi, ti) as t:
+            for trial in range(6):
+                sched = rng.integers(0, 3, size=int(rng.integers(1, 9)))
+                t.set_schedule(sched)
+                check(t, lvl, st, alpha, f"scripted{list(sched)}", t.run("scripted"))
+
+
+def test_random_graphs_with_duplicates_and_loops():
+    P = _P()
+    rng = np.random.default_rng(11)
+    for trial in range(8):
+        n = int(rng.integers(50, 3000))
+        m = int(rng.integers(0, 4 * n))
+        src = rng.integers(0, n, m)
+        dst = rng.integers(0, n, m)
+        order = np.argsort(src, kind="stable")
+        src, dst = src[order], dst[order]
+        off = np.zeros(n + 1, np.uint32)
+        np.add.at(off, src + 1, 1)
+        off = np.cumsum(off).astype(np.uint32)
+        tgt = dst.astype(np.uint32)
+        lvl, st, alpha = oracle.peel(off, tgt)
+        with P.Trimmer(off, tgt) as t:
+            for v in VARIANTS:
+                check(t, lvl, st, alpha, v, t.run(v))
+
+
+def test_round_log_and_stats():
+    P = _P()
+    g = cfg.config_small(2)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    off, tgt = dev_csr(g)
+    oi, ti = dev_csr_in(g)
+    with P.Trimmer(off, tgt, oi, ti, flags=P.TRIM_FLAG_ROUND_LOG | P.TRIM_FLAG_STATS) as t:
+        s = t.run("heuristic")
+        check(t, lvl, st, alpha, "heuristic", s)
+        log = t.round_log()
+        assert len(log) == alpha
+        hist = np.bincount(lvl[lvl != P.TRIM_LIVE].astype(np.int64))
+        for rec in log:
+            assert rec.removed == (hist[rec.round] if rec.round < len(hist) else 0)
+            assert rec.frontier == hist[rec.round - 1]
+            assert rec.t_end_ns >= rec.t_start_ns
+        assert sum(s["rounds_by_variant"]) == alpha
+
+
+def test_timeout_is_reported_and_context_recovers():
+    """A 1 ns bound on every device wait makes the first grid barrier give up:
+    the run returns TRIM_ERR_TIMEOUT (no fault, no hang) and the context keeps
+    working with the normal bound."""
+    P = _P()
+    g = cfg.config_small(1)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    off, tgt = dev_csr(g)
+    with P.Trimmer(off, tgt) as t:
+        normal = t.params()["spin_limit_ns"]
+        t.set_params(spin_limit_ns=1)
+        with pytest.raises(P.TrimError) as e:
+            t.run("ac6")
+        assert e.value.code == 6
+        t.set_params(spin_limit_ns=normal)
+        check(t, lvl, st, alpha, "ac6", t.run("ac6"))
+
+
+@pytest.mark.parametrize("i", [0, 1, 2])
+def test_full_configs_all_variants(i):
+    """Full-size workloads (planted n=1e5, R-MAT scale 22, deep cascade 2^24):
+    every vertex compared with the oracle, in the launch configuration the
+    benchmark uses."""
+    P = _P()
+    g = cfg.config(i)
+    oi_np, ti_np = oracle.transpose(g.off, g.tgt)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt, (oi_np, ti_np))
+    off, tgt = dev_csr(g)
+    import torch
+    oi = torch.from_numpy(oi_np.astype(np.int32)).cuda()
+    ti = torch.from_numpy(ti_np.astype(np.int32)).cuda()
+    variants = ["ac4"] if i == 0 else VARIANTS
+    with P.Trimmer(off, tgt, oi, ti) as t:
+        for v in variants:
+            check(t, lvl, st, alpha, v, t.run(v))
