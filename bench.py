@@ -1,0 +1,415 @@
+"""Benchmark: trimming throughput (edges/s = m / trim time) on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config I] [--variant V] [--sweep]
+
+A step is one complete trimming (every round, from the initial sink pass to the
+empty frontier) of the R-MAT scale-22 workload (configs index 1: 4,194,304
+vertices, edge factor 16, 10% sinks) with inputs resident in HBM; the L2 cache
+is flushed before every step and the step is timed with CUDA events on the
+library's stream. Rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle (sequential queue peeling, Algorithm 5
+run one step at a time) on the host on the same workload.
+N > 1: independent replicas, one per GPU (trimming one graph has no sharded
+form here; see the design notes), value = edges of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "edges/s (m/trim time) at 1 GB300, % HBM roofline; learned/batched vs fixed schedule"
+UNIT = "edges/s"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trim_persistent_kernel_rmat22.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2107_12720_gb300", "csrc", "trim_kernels.cu")
+
+
+# ---------------------------------------------------------------- workload
+
+def workload(idx: int):
+    import graphgen.configs as cfg
+    g = cfg.config(idx)
+    names = {0: "planted_trim n=100,000 (C 30k / R 30k / T 40k), seed 1",
+             1: "rmat22: R-MAT scale 22 (n=4,194,304), edge factor 16, a/b/c=.57/.19/.19, "
+                "ids permuted, dedup, no self-loops, 10% sinks, seed 2",
+             2: "deep_cascade n=2^24: C 10% / R 20% / T 70% as 4,096 chains (~2,867 deep), "
+                "mean out-degree 8, seed 3",
+             3: "batched: 4,096 planted graphs, log-normal sizes (median 2,000, sigma 1.5), seed 4",
+             4: "large_mixed: R-MAT scale 26 + 2^25 planted block (chains ~10,000 deep), seed 5"}
+    return g, names[idx]
+
+
+def host_transpose(off: np.ndarray, tgt: np.ndarray):
+    """G^T as plain data preparation (stable counting sort by target)."""
+    n = off.shape[0] - 1
+    src = np.repeat(np.arange(n, dtype=np.uint32), np.diff(off.astype(np.int64)))
+    order = np.argsort(tgt, kind="stable")
+    tgt_in = src[order]
+    off_in = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(tgt, minlength=n), out=off_in[1:])
+    return off_in.astype(np.uint32), tgt_in.astype(np.uint32)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, period_ms: int = 100):
+        self.dev = device_index
+        self.period = period_ms
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.6)
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.count(",") >= 8]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(name)
+        # samples under load: the upper half of the observed clocks (the run keeps the GPU busy)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline
+
+def algorithmic_bytes(n: int, st: dict, variant_flags: dict) -> int:
+    """Bytes the method must move in one run (per-unit figures of the design
+    notes): init 12n; per removed vertex 20 B (log write + read, level write,
+    G^T offsets); AC-4 12 B per in-edge (id read + 8-byte atomic read-modify-
+    write); AC-3 12 B per live-list entry swept plus 4 B per survivor written;
+    AC-6 24 B per supporting-set member re-scanned; 8 B per out-edge inspected
+    (target id + its level)."""
+    D = st["n_dead"]
+    b = 12 * n + 20 * D
+    b += 12 * st["in_edges_pushed"]
+    b += 16 * st["live_swept"]
+    b += 24 * st["candidates"]
+    b += 8 * st["edges_inspected"]
+    return int(b)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the persistent kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    kv = {}
+    for line in open(PROFILE_TRAFFIC):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    try:
+        return int(float(kv["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    """Maximum of a per-rank scalar over all ranks (the slowest rank's time)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, ws: int) -> float:
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(g, seconds: float = 12.0) -> dict:
+    """The oracle (sequential C, one thread) on the same graph, G^T prepared
+    outside the timing, repeated for about `seconds`."""
+    import oracle
+    oi, ti = oracle.transpose(g.off, g.tgt)
+    times = []
+    t_end = time.perf_counter() + seconds
+    while time.perf_counter() < t_end or len(times) < 3:
+        t0 = time.perf_counter()
+        oracle.peel(g.off, g.tgt, (oi, ti))
+        times.append(time.perf_counter() - t0)
+    mean = statistics.mean(times)
+    return {"value": g.m / mean, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the full workload graph, {len(times)} repeats of the single-threaded "
+                      f"oracle peel (G^T prepared once outside the timing), mean {mean * 1e3:.1f} ms",
+            "cpu": cpu_name(), "nproc": os.cpu_count()}
+
+
+def cpu_name() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    import oracle
+    g, wname = workload(args.config)
+    oi, ti = oracle.transpose(g.off, g.tgt)
+    for _ in range(args.warmup):
+        oracle.peel(g.off, g.tgt, (oi, ti))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.peel(g.off, g.tgt, (oi, ti))
+    dt = time.perf_counter() - t0
+    value = g.m * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": wname, "n": g.n, "m": g.m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the full workload graph per step, {args.steps} steps",
+                             "cpu": cpu_name(), "nproc": os.cpu_count()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def time_variant(P, t, variant, steps, warmup, flush_buf):
+    import torch
+    stream = t.stream
+    for _ in range(warmup):
+        t.run(variant)
+    times, kern = [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    last = None
+    for _ in range(steps):
+        flush_buf.add_(1)  # writes more than the L2 holds, on the same stream
+        e0.record(stream)
+        t.run_async(variant)
+        e1.record(stream)
+        last = t.sync()
+        times.append(e0.elapsed_time(e1))
+        kern.append(last["device_ms"])
+    return times, kern, last
+
+
+def e2e_measure(P, g, off_in, tgt_in, variant, steps):
+    """Through the C ABI with host buffers: trim_create copies the pinned host
+    CSR (and G^T) to the device, trim_run trims, trim_level copies the levels
+    back; all inside the host wall-clock timing."""
+    import torch
+    pin = lambda a: torch.from_numpy(a.view(np.int32)).pin_memory()
+    ho, ht, hoi, hti = pin(g.off), pin(g.tgt), pin(off_in), pin(tgt_in)
+    out = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    ts = []
+    for s in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with P.Trimmer(ho, ht, hoi, hti) as t:
+            t.run(variant)
+            P.trim_level(t.ctx, out.data_ptr(), 0)
+        t1 = time.perf_counter()
+        if s:  # the first call pays one-time costs (module load, context)
+            ts.append(t1 - t0)
+    h2d = (g.off.nbytes + g.tgt.nbytes + off_in.nbytes + tgt_in.nbytes)
+    return g.m / statistics.mean(ts), h2d, out.numel() * 4
+
+
+def run_ours(args, rank, ws, local):
+    import torch
+    import paper_2107_12720_gb300 as P
+    torch.cuda.set_device(local)
+    g, wname = workload(args.config)
+    off_in, tgt_in = host_transpose(g.off, g.tgt)
+    dev = lambda a: torch.from_numpy(a.view(np.int32)).cuda()
+    d_off, d_tgt, d_oi, d_ti = dev(g.off), dev(g.tgt), dev(off_in), dev(tgt_in)
+    flush = torch.empty(256 << 20 >> 2, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    t = P.Trimmer(d_off, d_tgt, d_oi, d_ti, stream=stream, flags=P.TRIM_FLAG_STATS)
+    model = os.path.join(ROOT, "paper_2107_12720_gb300", "models", "scheduler_mlp.npy")
+    have_model = os.path.exists(model)
+    if have_model:
+        t.set_model(np.load(model))
+    headline = args.variant or ("learned" if have_model else "heuristic")
+
+    sweep = {}
+    if args.sweep and rank == 0:
+        for v in ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if have_model else []):
+            ts, ks, st = time_variant(P, t, v, max(20, args.steps // 10), 3, flush)
+            sweep[v] = {"ms": statistics.mean(ts), "kernel_ms": statistics.mean(ks),
+                        "edges_per_s": g.m / (statistics.mean(ts) * 1e-3),
+                        "rounds_by_variant": st["rounds_by_variant"]}
+            print(f"# {v:10s} {statistics.mean(ts):8.4f} ms  kernel {statistics.mean(ks):8.4f} ms"
+                  f"  {g.m / statistics.mean(ts) / 1e-3:.3e} edges/s  rounds {st['rounds_by_variant']}",
+                  file=sys.stderr, flush=True)
+
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    for _ in range(args.warmup):
+        t.run(headline)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ts, ks, st = time_variant(P, t, headline, args.steps, 0, flush)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop() if rank == 0 else None
+    step_s = statistics.mean(ts) * 1e-3
+    total_s = max_over_ranks(sum(ts) * 1e-3, ws)
+    edges_total = sum_over_ranks(float(g.m) * args.steps, ws)
+    value = edges_total / total_s
+    kernel_ms = statistics.mean(ks)
+
+    e2e = None
+    if rank == 0 and args.e2e_steps > 0:
+        ev, h2d, d2h = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps)
+        e2e = {"value": ev * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    t.close()
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    alg = algorithmic_bytes(g.n, st, {})
+    achieved = alg / (kernel_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wname, "n": g.n, "m": g.m, "schedule": headline,
+                   "rounds": st["rounds"], "rounds_by_variant": st["rounds_by_variant"],
+                   "l2": "flushed before every step (256 MB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                   "timing": "CUDA events on the library stream around reset + persistent kernel"},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "kernel": "trim_persistent_kernel", "kernel_ms": kernel_ms,
+                     "algorithmic_bytes": alg, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s"},
+    }
+    if sweep:
+        line["variants"] = sweep
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--variant", default=None)
+    ap.add_argument("--sweep", action="store_true", help="also time every variant (stderr + JSON)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    rank, ws, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -87,10 +87,8 @@ typedef struct {
 
 /* Tunables (filled by the autotuner; defaults are sensible). */
 typedef struct {
-  uint32_t block_threads;     /* threads per CTA of the persistent kernel (128..1024, x32) */
+  uint32_t block_threads;     /* threads per CTA of the persistent kernel (128..512, x32)  */
   uint32_t ctas_per_sm;       /* persistent CTAs per SM (0 = as many as fit)               */
-  uint32_t big_degree;        /* AC-4: in-degree above which a vertex is split into pieces  */
-  uint32_t piece_edges;       /* AC-4: edges per piece of a big vertex                      */
   uint32_t batch_cta_max_n;   /* batched: graphs with at most this many vertices run in
                                  one CTA (0 = never)                                         */
   uint32_t batch_cta_max_m;   /* batched: ... and at most this many edges                   */

@@ -16,7 +16,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtrim.so")
-SOURCES = ["trim_kernels.cu", "trim_api.cu", "mlp.cu"]
+# (source, extra nvcc flags, object): the persistent kernel is built once per
+# flavour (variant set), see TRIM_MODES in trim_kernels.cu
+UNITS = [("trim_kernels.cu", ["-DTRIM_MODES=1"], "trim_kernels_m1.o"),
+         ("trim_kernels.cu", ["-DTRIM_MODES=2"], "trim_kernels_m2.o"),
+         ("trim_kernels.cu", ["-DTRIM_MODES=4"], "trim_kernels_m4.o"),
+         ("trim_kernels.cu", ["-DTRIM_MODES=15"], "trim_kernels_m15.o"),
+         ("trim_aux.cu", [], "trim_aux.o"),
+         ("trim_api.cu", [], "trim_api.o"),
+         ("mlp.cu", [], "mlp.o")]
+SOURCES = sorted({u[0] for u in UNITS})
 HEADERS = ["trim_internal.cuh", os.path.join("..", "..", "include", "trim.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
@@ -41,10 +50,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     procs = []
     objs = []
-    for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+    for src, extra, o in UNITS:
+        obj = os.path.join(BUILD, o)
         objs.append(obj)
-        cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -39,8 +39,7 @@ struct trim_ctx {
   uint32_t *level = nullptr, *cnt = nullptr, *supp = nullptr, *s_head = nullptr,
            *s_next = nullptr, *s_cnt = nullptr, *s_off = nullptr, *s_list = nullptr,
            *log = nullptr, *roff = nullptr, *live0 = nullptr, *live1 = nullptr, *bsum = nullptr;
-  uint2 *pieces0 = nullptr, *pieces1 = nullptr;
-  uint32_t piece_cap = 0;
+  uint32_t *w4_row = nullptr, *w4_eoff = nullptr, *chunk_first = nullptr;
   Ctrl* ctrl = nullptr;
   Ctrl* h_ctrl = nullptr;  // pinned host mirror for read-back
   trim_round_rec_t* rlog = nullptr;
@@ -51,7 +50,7 @@ struct trim_ctx {
   uint32_t script_len = 0;
   uint8_t* status_tmp = nullptr;
   trim_params_t params{};
-  int grid = 0;
+  int grids[4] = {0, 0, 0, 0};
   bool ran = false;
   bool pending = false;
   bool s_cnt_dirty = false;
@@ -134,8 +133,6 @@ trim_err_t check_device(trim_ctx* c, int* dev, int* sms) {
 void default_params(trim_params_t* p) {
   p->block_threads = 512;
   p->ctas_per_sm = 0;
-  p->big_degree = 1024;
-  p->piece_edges = 256;
   p->batch_cta_max_n = 4096;
   p->batch_cta_max_m = 65536;
   p->spin_limit_ns = 5ull * 1000 * 1000 * 1000;  // 5 s
@@ -143,13 +140,30 @@ void default_params(trim_params_t* p) {
   p->heur_ac6_ratio = 1.0f;
 }
 
+// per-warp append slices in dynamic shared memory: 4 buffers (dead log, AC-4
+// work-list rows and edge offsets, AC-3 live list) of kSliceEntries words per
+// warp, sized for the largest block (512 threads = 16 warps)
+constexpr uint32_t kSliceEntries = 256;
+constexpr uint32_t kSbufCap = kSliceEntries;
+size_t dyn_smem_bytes() { return 16 * 4 * (size_t)kSliceEntries * sizeof(uint32_t); }
+
+// kernel flavours: index 0..3 = AC-4 only, AC-6 only, AC-3 only, everything
+typedef void (*persistent_fn)(trimk::Dev);
+const persistent_fn kFlavours[4] = {trim_persistent_kernel_m1, trim_persistent_kernel_m2,
+                                    trim_persistent_kernel_m4, trim_persistent_kernel_m15};
+
 trim_err_t compute_grid(trim_ctx* c) {
-  int per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trim_persistent_kernel,
-                                                   (int)c->params.block_threads, 0));
-  if (per_sm <= 0) return fail(c, TRIM_ERR_INVALID_ARG, "block_threads does not fit on an SM");
-  if (c->params.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)c->params.ctas_per_sm);
-  c->grid = per_sm * c->sm_count;
+  for (int k = 0; k < 4; ++k) {
+    int per_sm = 0;
+    CK(cudaFuncSetAttribute(kFlavours[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)dyn_smem_bytes()));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kFlavours[k],
+                                                     (int)c->params.block_threads,
+                                                     dyn_smem_bytes()));
+    if (per_sm <= 0) return fail(c, TRIM_ERR_INVALID_ARG, "block_threads does not fit on an SM");
+    if (c->params.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)c->params.ctas_per_sm);
+    c->grids[k] = per_sm * c->sm_count;
+  }
   return TRIM_OK;
 }
 
@@ -322,17 +336,13 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
   return TRIM_OK;
 }
 
-// pieces of big vertices: at most m/big + m/piece per round, two rounds kept
-trim_err_t ensure_pieces(trim_ctx* c) {
-  const uint64_t need =
-      c->m / std::max<uint32_t>(1, c->params.big_degree) + c->m / c->params.piece_edges + 16;
-  if (c->pieces0 && c->piece_cap >= need) return TRIM_OK;
-  uint2 *a = nullptr, *b = nullptr;
-  TRY(dalloc(c, &a, need));
-  TRY(dalloc(c, &b, need));
-  c->pieces0 = a;
-  c->pieces1 = b;
-  c->piece_cap = (uint32_t)std::min<uint64_t>(need, 0xFFFFFFFFu);
+// AC-4 work list (one entry per removed vertex with in-edges) and the owner
+// index of every 32-edge chunk of its in-edge prefix; allocated on first use.
+trim_err_t ensure_work_list(trim_ctx* c) {
+  if (c->w4_row) return TRIM_OK;
+  TRY(dalloc(c, &c->w4_row, c->n));
+  TRY(dalloc(c, &c->w4_eoff, c->n));
+  TRY(dalloc(c, &c->chunk_first, (c->m >> 5) + 2));
   return TRIM_OK;
 }
 
@@ -365,7 +375,7 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
     }
     if (ac4 && c->ioff == nullptr) TRY(build_transpose(c));
   }
-  if (ac4) { f |= trimk::F_AC4_POSSIBLE; TRY(ensure_pieces(c)); }
+  if (ac4) { f |= trimk::F_AC4_POSSIBLE; TRY(ensure_work_list(c)); }
   if (ac6) f |= trimk::F_AC6_POSSIBLE;
   if (ac3) f |= trimk::F_AC3_POSSIBLE;
   if (c->n == 0) {
@@ -388,23 +398,28 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
   D.level = c->level; D.cnt = c->cnt; D.supp = c->supp;
   D.s_head = c->s_head; D.s_next = c->s_next; D.s_cnt = c->s_cnt; D.s_off = c->s_off;
   D.s_list = c->s_list; D.log = c->log; D.roff = c->roff; D.live0 = c->live0;
-  D.live1 = c->live1; D.pieces0 = c->pieces0; D.pieces1 = c->pieces1;
-  D.piece_cap = c->piece_cap; D.bsum = c->bsum; D.C = c->ctrl;
+  D.live1 = c->live1; D.w4_row = c->w4_row; D.w4_eoff = c->w4_eoff;
+  D.chunk_first = c->chunk_first; D.bsum = c->bsum; D.C = c->ctrl;
+  D.sbuf_cap = kSbufCap;
   D.rlog = c->rlog; D.rlog_cap = c->rlog_cap;
   D.model = c->has_model ? c->model : nullptr;
   D.script = c->script; D.script_len = c->script_len;
   D.mode = variant; D.flags = f;
-  D.big_degree = c->params.big_degree; D.piece_edges = c->params.piece_edges;
   D.spin_limit_ns = c->params.spin_limit_ns;
   D.heur_push_ratio = c->params.heur_push_ratio;
   D.heur_ac6_ratio = c->params.heur_ac6_ratio;
-  if ((uint32_t)c->grid > 8192) return fail(c, TRIM_ERR_INVALID_ARG, "grid too large");
-  CK(cudaEventRecord(c->ev0, c->stream));
-  trim_reset_ctrl_kernel<<<1, 32, 0, c->stream>>>(c->ctrl, c->m);
+  // the lean single-variant flavours unless features or a per-round schedule are needed
+  int flavour = 3;
+  if (!(f & trimk::F_NEED_FEATURES) && variant <= TRIM_AC3_PULL) flavour = (int)variant;
+  const int grid = c->grids[flavour];
+  if ((uint32_t)grid > 8192) return fail(c, TRIM_ERR_INVALID_ARG, "grid too large");
+  trim_reset_ctrl_kernel<<<1, 32, 0, c->stream>>>(c->ctrl);
   CK(cudaGetLastError());
+  CK(cudaEventRecord(c->ev0, c->stream));  // device_ms covers the persistent kernel alone
   void* args[] = {&D};
-  CK(cudaLaunchCooperativeKernel((const void*)trim_persistent_kernel, dim3(c->grid),
-                                 dim3(c->params.block_threads), args, 0, c->stream));
+  CK(cudaLaunchCooperativeKernel((const void*)kFlavours[flavour], dim3(grid),
+                                 dim3(c->params.block_threads), args, dyn_smem_bytes(),
+                                 c->stream));
   CK(cudaEventRecord(c->ev1, c->stream));
   c->pending = true;
   c->last_mode = variant;
@@ -571,8 +586,6 @@ trim_err_t trim_set_params(trim_ctx* c, const trim_params_t* p) {
   if (!c || !p) return fail(c, TRIM_ERR_INVALID_ARG, "null argument");
   if (p->block_threads < 128 || p->block_threads > 512 || p->block_threads % 32)
     return fail(c, TRIM_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [128,512]");
-  if (p->piece_edges < 32 || p->big_degree < 32)
-    return fail(c, TRIM_ERR_INVALID_ARG, "piece_edges and big_degree must be >= 32");
   if (p->spin_limit_ns == 0) return fail(c, TRIM_ERR_INVALID_ARG, "spin_limit_ns must be > 0");
   if (!(p->heur_push_ratio > 0.0f) || !(p->heur_ac6_ratio > 0.0f))
     return fail(c, TRIM_ERR_INVALID_ARG, "heuristic ratios must be > 0");
@@ -583,10 +596,6 @@ trim_err_t trim_set_params(trim_ctx* c, const trim_params_t* p) {
     c->params = old;
     compute_grid(c);
     return e;
-  }
-  if (p->big_degree != old.big_degree || p->piece_edges != old.piece_edges) {
-    c->pieces0 = c->pieces1 = nullptr;  // reallocated on the next AC-4 run (old ones freed at destroy)
-    c->piece_cap = 0;
   }
   return TRIM_OK;
 }

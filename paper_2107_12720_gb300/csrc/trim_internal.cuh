@@ -23,48 +23,56 @@ constexpr int NFEAT = 12;
 constexpr uint32_t F_STATS = TRIM_FLAG_STATS;
 constexpr uint32_t F_ROUND_LOG = TRIM_FLAG_ROUND_LOG;
 constexpr uint32_t F_NEED_FEATURES = 0x100;  // scheduler modes: gather per-frontier degrees
-constexpr uint32_t F_AC4_POSSIBLE = 0x200;   // counters must be initialised / big pieces kept
+constexpr uint32_t F_AC4_POSSIBLE = 0x200;   // counters initialised, AC-4 work list kept
 constexpr uint32_t F_AC6_POSSIBLE = 0x400;
 constexpr uint32_t F_AC3_POSSIBLE = 0x800;
 
-// Per-frontier accumulators, filled while F_r is appended (slot r & 3).
+// Per-round accumulators, filled while round r runs (ring slot r & 3). CTA 0
+// zeroes slot (k+2) & 3 at the start of round k: that slot was last read at the
+// start of round k-1 and is next written in round k+2.
 struct RoundStat {
   unsigned long long sum_in;   // sum of in-degrees of F_r
   unsigned long long sum_out;  // sum of out-degrees of F_r
   unsigned int hist[3];        // in-degree < 8, < 256, >= 256
-  unsigned int npieces;        // AC-4 pieces reserved for big vertices of F_r
+  unsigned int live_count;     // AC-3: survivors written to the output live list in round r
   unsigned int pad[2];
 };
 
-// Global control block. Barrier words sit on their own 128-byte lines.
+// Global control block. Counters hit by every CTA sit on their own 128-byte lines.
 struct Ctrl {
-  unsigned int bar_count; unsigned int _p0[31];
-  unsigned int bar_gen;   unsigned int _p1[31];
-  unsigned int log_len;   unsigned int _p2[31];
-  unsigned int live_len[2]; unsigned int live_fill; unsigned int _p3[29];
-  // written only by the barrier hook (one warp), read by everyone after a barrier
-  unsigned int round;      // current round r (1-based once the loop runs)
-  unsigned int f_begin;    // F_{r-1} = log[f_begin, f_end)
-  unsigned int f_end;
-  unsigned int variant;    // variant of round r (0..2)
-  unsigned int prev_variant;  // variant of round r-1 (NIL before the first round)
-  unsigned int c4;         // AC-4: decrements applied for log[0, c4)
-  unsigned int ac3_list;   // which live list holds the AC-3 superset (0/1), NIL = none yet
-  unsigned int done;
-  unsigned int err;
-  unsigned int err_info;
-  unsigned int rounds;     // alpha
+  unsigned int bar;       unsigned int _p0[31];  // monotone grid-barrier arrivals
+  unsigned int log_len;   unsigned int _p1[31];  // entries in the dead log
+  unsigned long long w4;  unsigned int _p1b[30];  // AC-4 work list: items (low 32) | edges (high 32)
+  unsigned int err;       unsigned int err_info; unsigned int _p2[30];
+  // published by CTA 0 for the host
+  unsigned int rounds;    // alpha
   unsigned int vcount[3];
   unsigned int rlog_len;
-  unsigned int _p4[15];
-  unsigned long long m_live;
-  unsigned long long t_release;   // %globaltimer when the current round was released
-  unsigned long long cum_in;      // sum of in-degrees over log[0, log_len)
-  unsigned long long cum_in_c4;   // ... over log[0, c4)
-  unsigned long long last_round_ns;
+  unsigned int _p3[27];
+  unsigned long long t_round[4];  // CTA 0's %globaltimer at the start of round r (ring)
   unsigned long long stats[4];    // edges inspected, in-edges pushed, candidates, live swept
-  float feat[NFEAT];              // features of the upcoming round
   RoundStat rs[4];
+};
+
+// The schedule state of the current round. Every CTA keeps its own copy in
+// shared memory and advances it from the same global inputs after each grid
+// barrier, so all copies stay identical without a serial hand-off.
+struct Sched {
+  uint32_t round;         // r
+  uint32_t fb, fe;        // F_{r-1} = log[fb, fe)
+  uint32_t variant;       // variant of round r
+  uint32_t prev_variant;  // variant of round r-1 (NIL before round 1)
+  uint32_t c4w;           // AC-4 work list entries [0, c4w) already pushed
+  uint32_t e_c4;          // ... their edges: [0, e_c4)
+  uint32_t w_end;         // work list entries / edges of vertices removed before round r
+  uint32_t e_end;
+  uint32_t ac3_list;      // live list (0/1) holding a superset of the live vertices, NIL = none
+  uint32_t live_in_len;   // its length
+  uint32_t live_out;      // output list of an AC-3 round
+  uint32_t done;
+  uint32_t fprev;         // frontier size of round r-1 (timing feature)
+  unsigned long long m_live;     // out-edges of live vertices
+  float feat[12];                // features that chose this round's variant
 };
 
 struct Dev {
@@ -86,10 +94,13 @@ struct Dev {
   uint32_t* roff;     // roff[r] = start of F_r in the log (n+2)
   uint32_t* live0;    // AC-3 live lists
   uint32_t* live1;
-  uint2* pieces0;     // AC-4 pieces of big vertices (by round parity)
-  uint2* pieces1;
-  uint32_t piece_cap;
+  // AC-4 work list: one entry per removed vertex with in-edges, in removal order:
+  // the start of its G^T row and the exclusive prefix of in-degrees (edge offset).
+  uint32_t* w4_row;
+  uint32_t* w4_eoff;
+  uint32_t* chunk_first;  // [c]: work-list entry that owns edge 32c of the prefix
   uint32_t* bsum;     // per-CTA scratch of the grid-wide scan
+  uint32_t sbuf_cap;  // entries of each CTA append buffer (dynamic shared memory)
   Ctrl* C;
   trim_round_rec_t* rlog;
   uint32_t rlog_cap;
@@ -98,8 +109,6 @@ struct Dev {
   uint32_t script_len;
   uint32_t mode;      // trim_variant_t requested
   uint32_t flags;
-  uint32_t big_degree;
-  uint32_t piece_edges;
   uint64_t spin_limit_ns;
   float heur_push_ratio;
   float heur_ac6_ratio;
@@ -158,9 +167,12 @@ __device__ __forceinline__ void set_error(const Dev& D, unsigned code, unsigned 
 
 }  // namespace trimk
 
-// kernels (defined in trim_kernels.cu, launched from trim_api.cu)
-__global__ void trim_persistent_kernel(trimk::Dev D);
-__global__ void trim_reset_ctrl_kernel(trimk::Ctrl* C, uint64_t m);
+// kernels (trim_kernels.cu, one flavour per variant set; trim_aux.cu), launched from trim_api.cu
+__global__ void trim_persistent_kernel_m1(trimk::Dev D);   // AC-4 only
+__global__ void trim_persistent_kernel_m2(trimk::Dev D);   // AC-6 only
+__global__ void trim_persistent_kernel_m4(trimk::Dev D);   // AC-3 only
+__global__ void trim_persistent_kernel_m15(trimk::Dev D);  // all variants + schedulers
+__global__ void trim_reset_ctrl_kernel(trimk::Ctrl* C);
 __global__ void trim_status_kernel(const uint32_t* level, uint32_t n, uint8_t* status);
 __global__ void trim_indeg_kernel(const uint32_t* tgt, uint64_t m, uint32_t n, uint32_t* cnt,
                                   uint32_t* bad);

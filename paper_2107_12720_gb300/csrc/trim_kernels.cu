@@ -3,8 +3,7 @@
 // One cooperative launch runs every round of the trimming of Guo & Sekerinski
 // (arXiv 2107.12720): round 0 removes the vertices without out-edges, round r
 // the vertices whose successors were all removed in rounds < r (Definition 2).
-// Between rounds a grid-wide barrier (bounded spin) hands control to one warp
-// that closes the round's books and picks the variant of the next round:
+// Each round runs one of three kernels, chosen per round:
 //
 //   AC-4 push   (Section 5, Algorithm 6): each removed vertex w decrements the
 //               out-degree counter of every predecessor through G^T; the atomic
@@ -22,94 +21,306 @@
 //
 // All three read "u removed before round r" as level[u] < r, so mixing them
 // round by round yields the same levels.
+//
+// Rounds end at a grid-wide barrier (a monotone arrival counter, bounded spin).
+// No CTA hands anything to another between rounds: every CTA advances its own
+// copy of the schedule state (Sched, in shared memory) from the same global
+// inputs, so the copies agree. Appends to the dead log and to the AC-3 live
+// list go to per-CTA shared-memory buffers and reach global memory with one
+// atomic per CTA per round.
 #include "trim_internal.cuh"
+
+// This file is compiled once per kernel flavour: TRIM_MODES is a bit set of the
+// variants the kernel can run (1 AC-4, 2 AC-6, 4 AC-3) plus 8 for the
+// per-round schedulers (features, heuristic, MLP, scripted lists). A fixed
+// variant gets a kernel with only its own path, hence fewer registers.
+#ifndef TRIM_MODES
+#define TRIM_MODES 15
+#endif
+#define TRIM_CAT2(a, b) a##b
+#define TRIM_CAT(a, b) TRIM_CAT2(a, b)
+#define TRIM_KERNEL TRIM_CAT(trim_persistent_kernel_m, TRIM_MODES)
 
 using namespace trimk;
 
 namespace {
 
+constexpr int MODES = TRIM_MODES;
+constexpr int M_AC4 = 1, M_AC6 = 2, M_AC3 = 4, M_SCHED = 8;
 constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int MAX_WARPS = 16;   // blockDim.x <= 512
+constexpr int WBUF = 64;        // per-warp staging of supporting-set members
 
-struct RoundInfo {
-  uint32_t round, fb, fe, variant, prev_variant, c4, ac3_list, live_fill, done, npieces_prev,
-      live_in_len;
-};
-
-// ------------------------------------------------------------------ counters
 struct Counters {
   unsigned long long edges = 0, pushed = 0, cand = 0, swept = 0;
 };
 
+// Per-warp append slices. Each warp buffers what it removes (and, in AC-3
+// rounds, what survives) in its own slice of shared memory; no shared atomics
+// and no CTA-wide synchronisation inside the variant loops. A full slice is
+// flushed by its warp alone; at the end of a round one CTA-wide flush moves
+// all slices with one global atomic per counter.
+constexpr uint32_t LW = 256;  // entries per warp slice (per buffer)
+struct WarpSlice {
+  uint32_t nlog, nw4, nedge, nlive;   // entries in the slices; edges of the w4 entries
+  uint32_t log_base, w4_base, edge_base, live_base;  // global bases at the CTA flush
+  unsigned long long sum_in, sum_out;
+  uint32_t hist[3];
+  uint32_t pad;
+};
+
+// Per-CTA shared state.
+struct Cta {
+  Sched S;
+  WarpSlice ws[MAX_WARPS];
+  unsigned epoch;  // grid barriers passed
+  unsigned err;
+  uint32_t wbuf[MAX_WARPS][WBUF];
+};
+
+// dynamic shared memory: per warp w, 4 slices of LW words at w * 4 * LW:
+// dead-log entries | work-list rows | work-list edge offsets (warp-local) | live-list entries
+extern __shared__ uint32_t dyn_smem[];
+__device__ __forceinline__ uint32_t* slice(unsigned warp, int which) {
+  return dyn_smem + (warp * 4u + (unsigned)which) * LW;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void red_relaxed_add(unsigned* p, unsigned v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // ------------------------------------------------------------------ appends
 
-__device__ __forceinline__ void reserve_pieces(const Dev& D, uint32_t u, uint32_t din,
-                                               uint32_t r) {
-  const uint32_t np = (din + D.piece_edges - 1) / D.piece_edges;
-  const uint32_t pb = atomicAdd(&D.C->rs[r & 3].npieces, np);
-  if (pb + np > D.piece_cap) {
-    set_error(D, TRIM_ERR_STATE, 0xA4);
-    return;
-  }
-  uint2* P = (r & 1) ? D.pieces1 : D.pieces0;
-  for (uint32_t q = 0; q < np; ++q) P[pb + q] = make_uint2(u, q);
+// Writes the chunk-owner index for work-list entry `pos` covering edges [es, ee):
+// every chunk start 32c in that range is owned by this entry.
+__device__ __forceinline__ void mark_chunks(const Dev& D, uint32_t pos, uint32_t es, uint32_t ee) {
+  for (uint32_t c = (es + 31u) >> 5; (c << 5) < ee; ++c) D.chunk_first[c] = pos;
 }
 
-// Warp-collective: lanes with pred append u to the dead log as a member of F_r
-// and set level[u] = r. One atomic per warp (warp-aggregated).
-__device__ __forceinline__ void append_dead(const Dev& D, bool pred, uint32_t u, uint32_t r) {
+// Warp-collective: copies this warp's slices to global memory at the given bases.
+__device__ __forceinline__ void copy_slices(const Dev& D, const WarpSlice& w, unsigned warp,
+                                            uint32_t* live_out) {
   const unsigned lane = lane_id();
+  const uint32_t* sl = slice(warp, 0);
+  const uint32_t* sr = slice(warp, 1);
+  const uint32_t* se = slice(warp, 2);
+  const uint32_t* sv = slice(warp, 3);
+  for (uint32_t i = lane; i < w.nlog; i += 32) D.log[w.log_base + i] = sl[i];
+  for (uint32_t i = lane; i < w.nw4; i += 32) {
+    const uint32_t eo = w.edge_base + se[i];
+    const uint32_t ee = w.edge_base + (i + 1 < w.nw4 ? se[i + 1] : w.nedge);
+    D.w4_row[w.w4_base + i] = sr[i];
+    D.w4_eoff[w.w4_base + i] = eo;
+    mark_chunks(D, w.w4_base + i, eo, ee);
+  }
+  for (uint32_t i = lane; i < w.nlive; i += 32) live_out[w.live_base + i] = sv[i];
+}
+
+// Warp-collective: a slice is full; the warp reserves global space on its own.
+__device__ __noinline__ void warp_flush(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out) {
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  WarpSlice& w = B.ws[warp];
+  if (lane == 0) {
+    if (w.nlog) {
+      w.log_base = atomicAdd(&D.C->log_len, w.nlog);
+      if (w.log_base + w.nlog > D.n) { set_error(D, TRIM_ERR_STATE, 0xD1); w.nlog = 0; }
+    }
+    if (w.nw4) {
+      const unsigned long long o = atomicAdd(
+          &D.C->w4, (unsigned long long)w.nw4 | ((unsigned long long)w.nedge << 32));
+      w.w4_base = (uint32_t)o;
+      w.edge_base = (uint32_t)(o >> 32);
+    }
+    if (w.nlive) {
+      w.live_base = atomicAdd(&D.C->rs[r & 3].live_count, w.nlive);
+      if (w.live_base + w.nlive > D.n) { set_error(D, TRIM_ERR_STATE, 0xD3); w.nlive = 0; }
+    }
+  }
+  __syncwarp();
+  const WarpSlice c = w;
+  copy_slices(D, c, warp, live_out);
+  __syncwarp();
+  if (lane == 0) w.nlog = w.nw4 = w.nedge = w.nlive = 0;
+  __syncwarp();
+}
+
+// Warp-collective: lanes with pred are removed in round r: level[u] = r and u
+// joins F_r in the dead log; if it has in-edges (and AC-4 may run) it also
+// joins the AC-4 work list with its G^T row and in-degree.
+__device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uint32_t u,
+                                            uint32_t r, uint32_t* live_out,
+                                            bool level_set = false) {
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned mask = __ballot_sync(FULL, pred);
   if (mask == 0u) return;
-  const unsigned leader = __ffs(mask) - 1;
-  unsigned base = 0;
-  if (lane == leader) {
-    base = atomicAdd(&D.C->log_len, (unsigned)__popc(mask));
-    if (base + (unsigned)__popc(mask) > D.n) set_error(D, TRIM_ERR_STATE, 0xD1);  // never: each
-  }                                                                           // vertex dies once
-  base = __shfl_sync(FULL, base, leader);
-  if (base + (unsigned)__popc(mask) > D.n) return;
-  const bool feats = (D.flags & F_NEED_FEATURES) != 0;
-  unsigned din = 0, dout = 0;
-  if (pred) {
-    D.log[base + __popc(mask & ((1u << lane) - 1u))] = u;
-    D.level[u] = r;
-    if (D.ioff != nullptr && (feats || (D.flags & F_AC4_POSSIBLE))) {
-      din = __ldg(&D.ioff[u + 1]) - __ldg(&D.ioff[u]);
-      if ((D.flags & F_AC4_POSSIBLE) && din > D.big_degree) reserve_pieces(D, u, din, r);
-    }
-    if (feats) dout = __ldg(&D.off[u + 1]) - __ldg(&D.off[u]);
+  const bool feats = (MODES & M_SCHED) && (D.flags & F_NEED_FEATURES);
+  const bool track = D.ioff != nullptr && (((MODES & M_AC4) && (D.flags & F_AC4_POSSIBLE)) || feats);
+  uint32_t row = 0, din = 0;
+  if (pred && track) {
+    row = __ldg(&D.ioff[u]);
+    din = __ldg(&D.ioff[u + 1]) - row;
   }
+  const bool w = (MODES & M_AC4) && pred && din > 0u && (D.flags & F_AC4_POSSIBLE);
+  const unsigned wmask = __ballot_sync(FULL, w);
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned k = __popc(mask), kw = __popc(wmask);
+  const unsigned ew = w ? din : 0u;
+  const unsigned eincl = warp_incl_scan(ew);
+  const unsigned esum = __shfl_sync(FULL, eincl, 31);
+  WarpSlice& ws = B.ws[warp];
+  if (ws.nlog + k > LW || ws.nw4 + kw > LW) warp_flush(D, B, r, live_out);
+  const uint32_t pl = ws.nlog, pw = ws.nw4, pe = ws.nedge;
+  if (pred) {
+    slice(warp, 0)[pl + __popc(mask & lt)] = u;
+    if (!level_set) D.level[u] = r;
+  }
+  if (w) {
+    const unsigned at = pw + __popc(wmask & lt);
+    slice(warp, 1)[at] = row;
+    slice(warp, 2)[at] = pe + eincl - ew;
+  }
+  unsigned long long s_in = 0, s_out = 0;
+  unsigned h0 = 0, h1 = 0;
   if (feats) {
-    const unsigned long long s_in = warp_sum<unsigned long long>(din);
-    const unsigned long long s_out = warp_sum<unsigned long long>(dout);
-    const unsigned h0 = __popc(__ballot_sync(FULL, pred && din < 8u));
-    const unsigned h1 = __popc(__ballot_sync(FULL, pred && din >= 8u && din < 256u));
-    const unsigned h2 = __popc(mask) - h0 - h1;
-    if (lane == leader) {
+    unsigned dout = 0;
+    if (pred) dout = __ldg(&D.off[u + 1]) - __ldg(&D.off[u]);
+    s_out = warp_sum<unsigned long long>(dout);
+    s_in = warp_sum<unsigned long long>(din);
+    h0 = __popc(__ballot_sync(FULL, pred && din < 8u));
+    h1 = __popc(__ballot_sync(FULL, pred && din >= 8u && din < 256u));
+  }
+  __syncwarp();
+  if (lane == 0) {
+    ws.nlog = pl + k;
+    ws.nw4 = pw + kw;
+    ws.nedge = pe + esum;
+    if (feats) {
+      ws.sum_in += s_in;
+      ws.sum_out += s_out;
+      ws.hist[0] += h0;
+      ws.hist[1] += h1;
+      ws.hist[2] += k - h0 - h1;
+    }
+  }
+  __syncwarp();
+}
+
+// Warp-collective append of survivors to the AC-3 output live list.
+__device__ __forceinline__ void append_live(const Dev& D, Cta& B, bool pred, uint32_t v,
+                                            uint32_t r, uint32_t* out_list) {
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned mask = __ballot_sync(FULL, pred);
+  if (mask == 0u) return;
+  const unsigned k = __popc(mask);
+  WarpSlice& ws = B.ws[warp];
+  if (ws.nlive + k > LW) warp_flush(D, B, r, out_list);
+  const uint32_t pv = ws.nlive;
+  if (pred) slice(warp, 3)[pv + __popc(mask & ((1u << lane) - 1u))] = v;
+  __syncwarp();
+  if (lane == 0) ws.nlive = pv + k;
+  __syncwarp();
+}
+
+// End of round r: moves every warp slice of the CTA to global memory with one
+// global atomic per counter (all threads of the CTA).
+__device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out) {
+  __syncthreads();
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (warp == 0) {
+    // exclusive prefix of the per-warp counts (lane i holds warp i)
+    const bool has = lane < nw;
+    const uint32_t a = has ? B.ws[lane].nlog : 0u, b = has ? B.ws[lane].nw4 : 0u,
+                   c = has ? B.ws[lane].nedge : 0u, d = has ? B.ws[lane].nlive : 0u;
+    const uint32_t ia = warp_incl_scan(a), ib = warp_incl_scan(b), ic = warp_incl_scan(c),
+                   id = warp_incl_scan(d);
+    const uint32_t ta = __shfl_sync(FULL, ia, 31), tb = __shfl_sync(FULL, ib, 31),
+                   tc = __shfl_sync(FULL, ic, 31), td = __shfl_sync(FULL, id, 31);
+    unsigned long long s_in = has ? B.ws[lane].sum_in : 0ull;
+    unsigned long long s_out = has ? B.ws[lane].sum_out : 0ull;
+    uint32_t h[3];
+    for (int i = 0; i < 3; ++i) h[i] = warp_sum(has ? B.ws[lane].hist[i] : 0u);
+    s_in = warp_sum(s_in);
+    s_out = warp_sum(s_out);
+    uint32_t lb = 0, wb = 0, eb = 0, vb = 0;
+    if (lane == 0) {
       RoundStat* rs = &D.C->rs[r & 3];
+      if (ta) {
+        lb = atomicAdd(&D.C->log_len, ta);
+        if (lb + ta > D.n) { set_error(D, TRIM_ERR_STATE, 0xD5); lb = 0xFFFFFFFFu; }
+      }
+      if (tb) {
+        const unsigned long long o =
+            atomicAdd(&D.C->w4, (unsigned long long)tb | ((unsigned long long)tc << 32));
+        wb = (uint32_t)o;
+        eb = (uint32_t)(o >> 32);
+      }
+      if (td) {
+        vb = atomicAdd(&rs->live_count, td);
+        if (vb + td > D.n) { set_error(D, TRIM_ERR_STATE, 0xD6); vb = 0xFFFFFFFFu; }
+      }
       if (s_in) atomicAdd(&rs->sum_in, s_in);
       if (s_out) atomicAdd(&rs->sum_out, s_out);
-      if (h0) atomicAdd(&rs->hist[0], h0);
-      if (h1) atomicAdd(&rs->hist[1], h1);
-      if (h2) atomicAdd(&rs->hist[2], h2);
+      for (int i = 0; i < 3; ++i)
+        if (h[i]) atomicAdd(&rs->hist[i], h[i]);
     }
+    lb = __shfl_sync(FULL, lb, 0);
+    wb = __shfl_sync(FULL, wb, 0);
+    eb = __shfl_sync(FULL, eb, 0);
+    vb = __shfl_sync(FULL, vb, 0);
+    if (has) {
+      WarpSlice& w = B.ws[lane];
+      w.log_base = lb + ia - a;
+      w.w4_base = wb + ib - b;
+      w.edge_base = eb + ic - c;
+      w.live_base = vb + id - d;
+      if (lb == 0xFFFFFFFFu) w.nlog = 0;
+      if (vb == 0xFFFFFFFFu) w.nlive = 0;
+    }
+  }
+  __syncthreads();
+  const WarpSlice c = B.ws[warp];
+  copy_slices(D, c, warp, live_out);
+  __syncwarp();
+  if (lane == 0) {
+    WarpSlice& w = B.ws[warp];
+    w.nlog = w.nw4 = w.nedge = w.nlive = 0;
+    w.sum_in = w.sum_out = 0;
+    w.hist[0] = w.hist[1] = w.hist[2] = 0;
   }
 }
 
-// Warp-collective append to an AC-3 live list.
-__device__ __forceinline__ void append_live(const Dev& D, bool pred, uint32_t v, uint32_t list) {
-  const unsigned lane = lane_id();
-  const unsigned mask = __ballot_sync(FULL, pred);
-  if (mask == 0u) return;
-  const unsigned leader = __ffs(mask) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(&D.C->live_len[list], (unsigned)__popc(mask));
-  base = __shfl_sync(FULL, base, leader);
-  if (base + (unsigned)__popc(mask) > D.n) {
-    if (lane == leader) set_error(D, TRIM_ERR_STATE, 0xD3);
-    return;
+// ------------------------------------------------------------------ grid barrier
+
+// Grid-wide barrier: each CTA adds one arrival to a monotone counter and waits
+// until all gridDim.x arrivals of this epoch are in. The wait is bounded by
+// spin_limit_ns; past it the run stops with TRIM_ERR_TIMEOUT. Returns false if
+// the run must stop (any error flag).
+__device__ bool grid_barrier(const Dev& D, Cta& B) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned target = (++B.epoch) * gridDim.x;
+    fence_acq_rel();
+    red_relaxed_add(&D.C->bar, 1u);
+    const uint64_t t0 = globaltimer();
+    while ((int)(ld_acquire(&D.C->bar) - target) < 0) {
+      if (globaltimer() - t0 > D.spin_limit_ns) {
+        set_error(D, TRIM_ERR_TIMEOUT, 1);
+        break;
+      }
+    }
+    B.err = ld_relaxed(&D.C->err);
   }
-  if (pred) (list ? D.live1 : D.live0)[base + __popc(mask & ((1u << lane) - 1u))] = v;
+  __syncthreads();
+  return B.err == 0u;
 }
 
 // ------------------------------------------------------------------ scans
@@ -177,55 +388,9 @@ __device__ __forceinline__ unsigned owner_of(unsigned excl, unsigned k) {
   return lo;
 }
 
-// ------------------------------------------------------------------ grid barrier
-
-__device__ void round_hook(const Dev& D);
-
-// Grid-wide barrier with a bounded spin. The last CTA to arrive runs the round
-// hook (one warp) before it releases the others. Returns false if the run must
-// stop (error flag set, including a timed-out wait).
-__device__ bool grid_sync(const Dev& D, bool with_hook) {
-  __shared__ unsigned s_err;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const unsigned lane = lane_id();
-    unsigned gen = 0, last = 0;
-    if (lane == 0) {
-      gen = ld_relaxed(&D.C->bar_gen);
-      __threadfence();
-      last = (atom_add_acqrel(&D.C->bar_count, 1u) == gridDim.x - 1) ? 1u : 0u;
-    }
-    last = __shfl_sync(FULL, last, 0);
-    if (last) {
-      __threadfence();
-      if (with_hook) round_hook(D);
-      __syncwarp();
-      if (lane == 0) {
-        D.C->bar_count = 0;
-        __threadfence();
-        red_release_add(&D.C->bar_gen, 1u);
-      }
-    } else if (lane == 0) {
-      const uint64_t t0 = globaltimer();
-      while (ld_acquire(&D.C->bar_gen) == gen) {
-        if (globaltimer() - t0 > D.spin_limit_ns) {
-          set_error(D, TRIM_ERR_TIMEOUT, 1);
-          break;
-        }
-      }
-    }
-    if (lane == 0) {
-      __threadfence();
-      s_err = ld_relaxed(&D.C->err);
-    }
-  }
-  __syncthreads();
-  return s_err == 0u;
-}
-
 // ------------------------------------------------------------------ scheduler
 
-__device__ float log2p1(double x) { return (float)log2(1.0 + x); }
+__device__ __forceinline__ float log2p1(float x) { return log2f(1.0f + x); }
 
 // Cost rule of TRIM_SCHED_HEURISTIC (work each variant would do next round, in
 // rough units of one random 32-byte access): AC-4 walks the in-edges of every
@@ -233,20 +398,17 @@ __device__ float log2p1(double x) { return (float)log2(1.0 + x); }
 // the first time); AC-6 re-scans the supporting sets of the last frontier
 // (about one member per removed vertex) or, on entry, rebuilds the sets of all
 // live vertices.
-__device__ uint32_t heuristic_choice(const Dev& D, volatile const Ctrl* C, uint32_t nF,
-                                     unsigned long long backlog_in, uint32_t backlog_items,
-                                     uint32_t n_live, uint32_t cur_variant) {
-  const bool has4 = D.ioff != nullptr && (D.flags & F_AC4_POSSIBLE);
+__device__ uint32_t heuristic_choice(const Dev& D, const Sched& L, uint32_t nF, uint32_t n_live,
+                                     uint32_t w_end, uint32_t e_end) {
   const float inf = 3.0e38f;
-  float c4 = has4 ? (float)backlog_in + 0.5f * (float)backlog_items : inf;
-  const uint32_t list = C->ac3_list;
-  const float sweep = (list == NIL) ? (float)D.n : (float)C->live_len[list];
+  float c4 = (float)(e_end - L.e_c4) + 0.5f * (float)(w_end - L.c4w);
+  const float sweep = (L.ac3_list == NIL) ? (float)D.n : (float)L.live_in_len;
   float c3 = 0.35f * sweep + 0.5f * (float)nF;
-  float c6 = (cur_variant == TRIM_AC6_SUPPORT) ? 2.0f * (float)nF
-                                               : 1.5f * (float)n_live + 0.25f * (float)D.n;
+  float c6 = (L.variant == TRIM_AC6_SUPPORT) ? 2.0f * (float)nF
+                                             : 1.5f * (float)n_live + 0.25f * (float)D.n;
   c4 *= D.heur_push_ratio;
   c6 *= D.heur_ac6_ratio;
-  if (!(D.flags & F_AC4_POSSIBLE)) c4 = inf;
+  if (!(D.flags & F_AC4_POSSIBLE) || D.ioff == nullptr) c4 = inf;
   if (!(D.flags & F_AC6_POSSIBLE)) c6 = inf;
   if (!(D.flags & F_AC3_POSSIBLE)) c3 = inf;
   if (c4 <= c3 && c4 <= c6) return TRIM_AC4_PUSH;
@@ -290,197 +452,183 @@ __device__ uint32_t mlp_choice(const Dev& D, const float* f, bool* in_range) {
   return best;
 }
 
-// Closes round r (r = 0 is the initial sink pass) and prepares round r+1.
-// Runs on one warp of the last CTA to reach the barrier, before it releases.
-__device__ void round_hook(const Dev& D) {
-  volatile Ctrl* C = D.C;  // every word may have been written by another SM
+// Warp 0 of every CTA, after the barrier that ends round r (r = 0: the initial
+// sink pass): closes round r in the CTA's copy of the schedule and prepares
+// round r+1. Reads only values that are final for every CTA at this point, so
+// all copies take the same decisions. CTA 0 also publishes results and logs.
+__device__ void advance(const Dev& D, Cta& B) {
   const unsigned lane = lane_id();
-  const uint32_t r = C->round;
-  const uint32_t len = C->log_len;
-  const uint32_t fs = C->f_end;  // F_r = log[fs, len)
-  const uint32_t nF = len - fs;
-  const uint64_t now = globaltimer();
-  const uint32_t var = C->variant;
-  RoundStat rsr;
-  rsr.sum_in = C->rs[r & 3].sum_in;
-  rsr.sum_out = C->rs[r & 3].sum_out;
-  for (int i = 0; i < 3; ++i) rsr.hist[i] = C->rs[r & 3].hist[i];
-  const uint32_t frontier_prev = fs - C->f_begin;
-  __syncwarp();
-  if (lane == 0) {
-    D.roff[r] = fs;
-    D.roff[r + 1] = len;
-    if (r >= 1) {
-      if (var <= 2u) C->vcount[var] += 1;
+  Ctrl* C = D.C;
+  Sched L = B.S;
+  const uint32_t r = L.round;
+  const RoundStat* rs = &C->rs[r & 3];
+  const uint32_t len = ld_relaxed(&C->log_len);
+  const unsigned long long w4 = ld_relaxed64(&C->w4);
+  const uint32_t live_count = ld_relaxed(&rs->live_count);
+  const uint32_t w_end = (uint32_t)w4, e_end = (uint32_t)(w4 >> 32);
+  const uint32_t nF = len - L.fe;  // |F_r|
+  const bool feats = (MODES & M_SCHED) && (D.flags & F_NEED_FEATURES);
+  const bool cta0 = blockIdx.x == 0 && lane == 0;
+  if (r >= 1) {
+    if (cta0) {
+      if (L.variant <= 2u) C->vcount[L.variant] += 1;
       if ((D.flags & F_ROUND_LOG) && D.rlog != nullptr && r - 1 < D.rlog_cap) {
         trim_round_rec_t* rec = &D.rlog[r - 1];
         rec->round = r;
-        rec->variant = var;
-        rec->frontier = frontier_prev;
+        rec->variant = L.variant;
+        rec->frontier = L.fe - L.fb;
         rec->removed = nF;
-        rec->t_start_ns = C->t_release;
-        rec->t_end_ns = now;
-        for (int i = 0; i < NFEAT; ++i) rec->features[i] = C->feat[i];
+        rec->t_start_ns = ld_relaxed64(&C->t_round[r & 3]);
+        rec->t_end_ns = globaltimer();
+        for (int i = 0; i < NFEAT; ++i) rec->features[i] = L.feat[i];
         C->rlog_len = r;
       }
-      if (var == TRIM_AC4_PUSH) {
-        C->c4 = fs;
-        C->cum_in_c4 = C->cum_in;
-      }
-      if (var == TRIM_AC3_PULL) C->ac3_list = C->live_fill;
     }
-    C->last_round_ns = now - C->t_release;
-    C->cum_in += rsr.sum_in;
-    C->m_live -= rsr.sum_out;
-    if (nF) C->rounds = r + 1;
-    if (nF == 0) C->done = 1;
+    if (L.variant == TRIM_AC4_PUSH) {  // pushed every work-list entry that existed before round r
+      L.c4w = L.w_end;
+      L.e_c4 = L.e_end;
+    }
+    if (L.variant == TRIM_AC3_PULL) {
+      L.ac3_list = L.live_out;
+      L.live_in_len = live_count;
+    }
   }
-  __syncwarp();
-  if (nF != 0) {
+  if (cta0) {
+    D.roff[r] = L.fe;
+    D.roff[r + 1] = len;
+    C->rounds = nF ? r + 1 : r;
+  }
+  if (nF == 0) {
+    L.done = 1;
+  } else {
     const uint32_t n_live = D.n - len;
-    const unsigned long long m_live = C->m_live;
     float f[NFEAT];
-    f[0] = log2p1(nF);
-    f[1] = log2p1((double)rsr.sum_in);
-    f[2] = log2p1((double)rsr.sum_out);
-    f[3] = log2p1(n_live);
-    f[4] = log2p1((double)m_live);
-    f[5] = (float)nF / (float)max(1u, n_live);
-    f[6] = (float)((double)rsr.sum_in / (double)max(1ull, m_live));
-    f[7] = (float)rsr.hist[0] / (float)nF;
-    f[8] = (float)rsr.hist[1] / (float)nF;
-    f[9] = (float)rsr.hist[2] / (float)nF;
-    f[10] = log2p1((double)C->last_round_ns / (double)max(1u, r >= 1 ? frontier_prev : D.n));
-    f[11] = (float)(r + 1) / (float)(r + 1 + 64);
-    const uint32_t cur = (r >= 1) ? var : NIL;
+    for (int i = 0; i < NFEAT; ++i) f[i] = 0.0f;
+    if (feats) {
+      const unsigned long long sum_in = ld_relaxed64(&rs->sum_in);
+      const unsigned long long sum_out = ld_relaxed64(&rs->sum_out);
+      const uint32_t h0 = ld_relaxed(&rs->hist[0]), h1 = ld_relaxed(&rs->hist[1]),
+                     h2 = ld_relaxed(&rs->hist[2]);
+      const unsigned long long t_r = ld_relaxed64(&C->t_round[r & 3]);
+      const unsigned long long t_rm1 = ld_relaxed64(&C->t_round[(r - 1) & 3]);
+      L.m_live -= sum_out;
+      f[0] = log2p1((float)nF);
+      f[1] = log2p1((float)sum_in);
+      f[2] = log2p1((float)sum_out);
+      f[3] = log2p1((float)n_live);
+      f[4] = log2p1((float)L.m_live);
+      f[5] = (float)nF / (float)max(1u, n_live);
+      f[6] = (float)sum_in / (float)max(1ull, L.m_live);
+      f[7] = (float)h0 / (float)nF;
+      f[8] = (float)h1 / (float)nF;
+      f[9] = (float)h2 / (float)nF;
+      // time of round r-1 per vertex of its frontier (CTA 0's clock, published to all)
+      f[10] = (r >= 2) ? log2p1((float)(t_r - t_rm1) / (float)max(1u, L.fprev)) : 0.0f;
+      f[11] = (float)(r + 1) / (float)(r + 1 + 64);
+    }
     uint32_t next;
-    if (D.mode <= TRIM_AC3_PULL) {
+    if (!(MODES & M_SCHED) || D.mode <= TRIM_AC3_PULL) {
       next = D.mode;
     } else if (D.mode == TRIM_SCHED_SCRIPTED) {
       next = D.script_len ? D.script[r % D.script_len] : 0u;
       if (next > 2u) next = TRIM_AC3_PULL;
       if (next == TRIM_AC4_PUSH && D.ioff == nullptr) next = TRIM_AC3_PULL;
     } else {
-      const unsigned long long backlog_in = C->cum_in - C->cum_in_c4;
-      const uint32_t backlog_items = len - C->c4;
-      next = heuristic_choice(D, C, nF, backlog_in, backlog_items, n_live, cur);
+      next = heuristic_choice(D, L, nF, n_live, w_end, e_end);
       if (D.mode == TRIM_SCHED_LEARNED && D.model != nullptr) {
         bool in_range = false;
         const uint32_t learned = mlp_choice(D, f, &in_range);
         if (in_range) next = learned;
       }
     }
-    if (lane == 0) {
-      C->prev_variant = cur;
-      C->variant = next;
-      C->round = r + 1;
-      C->f_begin = fs;
-      C->f_end = len;
-      volatile RoundStat* nx = &C->rs[(r + 1) & 3];
-      nx->sum_in = 0; nx->sum_out = 0;
-      nx->hist[0] = nx->hist[1] = nx->hist[2] = 0;
-      nx->npieces = 0;
-      for (int i = 0; i < NFEAT; ++i) C->feat[i] = f[i];
-      if (next == TRIM_AC3_PULL) {
-        const uint32_t out = (C->ac3_list == NIL) ? 0u : (C->ac3_list ^ 1u);
-        C->live_fill = out;
-        C->live_len[out] = 0;
-      }
-    }
+    L.prev_variant = (r >= 1) ? L.variant : NIL;
+    L.fprev = L.fe - L.fb;  // frontier of round r, for the timing feature two rounds on
+    L.variant = next;
+    L.round = r + 1;
+    L.fb = L.fe;
+    L.fe = len;
+    L.w_end = w_end;
+    L.e_end = e_end;
+    if (next == TRIM_AC3_PULL) L.live_out = (L.ac3_list == NIL) ? 0u : (L.ac3_list ^ 1u);
+    for (int i = 0; i < NFEAT; ++i) L.feat[i] = f[i];
   }
-  if (lane == 0) C->t_release = globaltimer();
+  __syncwarp();
+  if (lane == 0) B.S = L;
+}
+
+// CTA 0, start of round k: timestamp, and zero the accumulator slot of round k+2.
+__device__ __forceinline__ void start_round(const Dev& D, uint32_t k) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.C->t_round[k & 3] = globaltimer();
+    RoundStat* z = &D.C->rs[(k + 2) & 3];
+    z->sum_in = 0; z->sum_out = 0;
+    z->hist[0] = z->hist[1] = z->hist[2] = 0;
+    z->live_count = 0;
+  }
 }
 
 // ------------------------------------------------------------------ AC-4
 
-// Warp-balanced in-edge walk over the removed vertices log[a, b): every warp
-// takes G consecutive entries and spreads their in-edges over its lanes
-// (a warp prefix sum of the degrees plus a shuffle search for the owner).
-// Vertices above big_degree are skipped when skip_big (they come as pieces).
-__device__ void ac4_items(const Dev& D, uint32_t a, uint32_t b, uint32_t r, bool skip_big,
-                          uint32_t gwarp, uint32_t nwarps, Counters& K) {
-  const unsigned lane = lane_id();
-  const uint32_t N = b - a;
-  const uint32_t G = min(32u, max(1u, (N + nwarps - 1) / nwarps));
-  for (uint32_t base = a + gwarp * G; base < b; base += nwarps * G) {
-    const uint32_t item = base + lane;
-    const bool has = lane < G && item < b;
-    uint32_t s = 0, d = 0;
-    if (has) {
-      const uint32_t w = ldcg(&D.log[item]);
-      s = __ldg(&D.ioff[w]);
-      d = __ldg(&D.ioff[w + 1]) - s;
-      if (skip_big && d > D.big_degree) d = 0;
-    }
-    const unsigned incl = warp_incl_scan(d);
-    const unsigned total = __shfl_sync(FULL, incl, 31);
-    const unsigned excl = incl - d;
-    for (unsigned k0 = 0; k0 < total; k0 += 64) {
-      uint32_t u[2], old[2];
-      bool v[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const unsigned k = k0 + q * 32 + lane;
-        v[q] = k < total;
-        const unsigned j = owner_of(excl, k);
-        const unsigned sj = __shfl_sync(FULL, s, j), ej = __shfl_sync(FULL, excl, j);
-        u[q] = v[q] ? __ldg(&D.itgt[sj + (k - ej)]) : 0u;
-      }
-#pragma unroll
-      for (int q = 0; q < 2; ++q) old[q] = v[q] ? atomicSub(&D.cnt[u[q]], 1u) : 0u;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        K.pushed += v[q] ? 1 : 0;
-        const bool pred = v[q] && old[q] == 1u && ldcg(&D.level[u[q]]) == LIVE;
-        append_dead(D, pred, u[q], r);
-      }
-    }
-  }
-}
-
-__device__ void ac4_round(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint32_t nwarps,
+// AC-4 push: decrement the counters of the predecessors of every removed vertex
+// not yet pushed, i.e. the in-edges [e_c4, e_end) of the work list. The edges are
+// cut into 32-edge chunks and each warp takes an equal run of chunks, so a hub's
+// in-edges spread over many warps. The owner of a chunk's first edge comes from
+// chunk_first; the next 31 work-list entries own the rest of the chunk (every
+// entry has at least one edge), and a shuffle search finds each lane's owner.
+__device__ void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, uint32_t nwarps,
                           Counters& K) {
+  constexpr int U = 4;  // chunks in flight per warp
   const unsigned lane = lane_id();
-  const uint32_t r = R.round;
-  if (R.c4 < R.fb) ac4_items(D, R.c4, R.fb, r, false, gwarp, nwarps, K);  // catch-up
-  ac4_items(D, R.fb, R.fe, r, true, gwarp, nwarps, K);
-  // pieces of the big vertices of F_{r-1}, reserved when they were appended
-  const uint2* P = ((r - 1) & 1) ? D.pieces1 : D.pieces0;
-  const uint32_t PE = D.piece_edges;
-  for (uint32_t p = gwarp; p < R.npieces_prev; p += nwarps) {
-    const uint32_t w = ldcg(&P[p].x), q = ldcg(&P[p].y);
-    const uint32_t s0 = __ldg(&D.ioff[w]), e0 = __ldg(&D.ioff[w + 1]);
-    const uint32_t s = s0 + q * PE, e = min(e0, s + PE);
-    for (uint32_t k0 = s; k0 < e; k0 += 64) {
-      uint32_t u[2], old[2];
-      bool v[2];
+  const uint32_t r = S.round;
+  // a vertex whose counter reaches zero is still live unless another variant ran
+  const bool check = D.mode != TRIM_AC4_PUSH;
+  const uint32_t ea = S.e_c4, eb = S.e_end, ia = S.c4w, ib = S.w_end;
+  if (eb <= ea) return;
+  const uint32_t c0 = ea >> 5, c1 = (eb + 31u) >> 5;
+  const uint32_t per = (c1 - c0 + nwarps - 1) / nwarps;
+  const uint32_t cb = c0 + gwarp * per, ce = min(c1, cb + per);
+  for (uint32_t c = cb; c < ce; c += U) {
+    const uint32_t cf = (lane < (unsigned)U && c + lane < ce) ? ldcg(&D.chunk_first[c + lane]) : 0u;
+    uint32_t wrow[U], weo[U], u[U], old[U];
+    bool valid[U];
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const uint32_t k = k0 + t * 32 + lane;
-        v[t] = k < e;
-        u[t] = v[t] ? __ldg(&D.itgt[k]) : 0u;
-      }
+    for (int q = 0; q < U; ++q) {
+      const uint32_t first = max(__shfl_sync(FULL, cf, q), ia);
+      const uint32_t ii = first + lane;
+      const bool in = c + q < ce && ii < ib;
+      wrow[q] = in ? ldcg(&D.w4_row[ii]) : 0u;
+      weo[q] = in ? ldcg(&D.w4_eoff[ii]) : 0xFFFFFFFFu;
+    }
 #pragma unroll
-      for (int t = 0; t < 2; ++t) old[t] = v[t] ? atomicSub(&D.cnt[u[t]], 1u) : 0u;
+    for (int q = 0; q < U; ++q) {
+      const uint32_t e = ((c + q) << 5) + lane;
+      valid[q] = c + q < ce && e >= ea && e < eb;
+      const unsigned j = owner_of(weo[q], e);
+      const uint32_t idx = __shfl_sync(FULL, wrow[q], j) + (e - __shfl_sync(FULL, weo[q], j));
+      u[q] = valid[q] ? __ldg(&D.itgt[idx]) : 0u;
+    }
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        K.pushed += v[t] ? 1 : 0;
-        const bool pred = v[t] && old[t] == 1u && ldcg(&D.level[u[t]]) == LIVE;
-        append_dead(D, pred, u[t], r);
-      }
+    for (int q = 0; q < U; ++q) old[q] = valid[q] ? atomicSub(&D.cnt[u[q]], 1u) : 0u;
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      K.pushed += valid[q] ? 1 : 0;
+      bool pred = valid[q] && old[q] == 1u;
+      if (pred && check) pred = ldcg(&D.level[u[q]]) == LIVE;
+      append_dead(D, B, pred, u[q], r, D.live0);
     }
   }
 }
 
 // ------------------------------------------------------------------ AC-3
 
-__device__ void ac3_round(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint32_t nwarps,
+__device__ void ac3_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, uint32_t nwarps,
                           Counters& K) {
   const unsigned lane = lane_id();
-  const uint32_t r = R.round;
-  const bool all = (R.ac3_list == NIL);
-  const uint32_t* Lin = (R.ac3_list == 1u) ? D.live1 : D.live0;
-  const uint32_t N = all ? D.n : R.live_in_len;
+  const uint32_t r = S.round;
+  const bool all = (S.ac3_list == NIL);
+  const uint32_t* Lin = (S.ac3_list == 1u) ? D.live1 : D.live0;
+  uint32_t* Lout = S.live_out ? D.live1 : D.live0;
+  const uint32_t N = all ? D.n : S.live_in_len;
   for (uint32_t base = gwarp * 32; base < N; base += nwarps * 32) {
     const uint32_t idx = base + lane;
     const bool has = idx < N;
@@ -499,8 +647,8 @@ __device__ void ac3_round(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint
     const bool stays = alive && !dies;
     if (stays && i != i0) D.supp[v] = i;
     K.swept += has ? 1 : 0;
-    append_dead(D, dies, v, r);
-    append_live(D, stays, v, R.live_fill);
+    append_dead(D, B, dies, v, r, Lout);
+    append_live(D, B, stays, v, r, Lout);
   }
 }
 
@@ -509,8 +657,8 @@ __device__ void ac3_round(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint
 // Warp-collective re-scan of members of a supporting set whose owner was
 // removed in round r-1: scan forward from the position after the lost support;
 // on success join the new support's set (intrusive list), else remove.
-__device__ __forceinline__ void ac6_rescan(const Dev& D, bool valid, uint32_t v, uint32_t r,
-                                           Counters& K) {
+__device__ __forceinline__ void ac6_rescan(const Dev& D, Cta& B, bool valid, uint32_t v,
+                                           uint32_t r, Counters& K) {
   const bool alive = valid && ldcg(&D.level[v]) == LIVE;
   uint32_t s = 0, d = 0, i = 0;
   bool resolved = true;
@@ -527,7 +675,7 @@ __device__ __forceinline__ void ac6_rescan(const Dev& D, bool valid, uint32_t v,
     D.s_next[v] = atomicExch(&D.s_head[t], v);
   }
   K.cand += valid ? 1 : 0;
-  append_dead(D, dies, v, r);
+  append_dead(D, B, dies, v, r, D.live0);
 }
 
 // Block-wide exclusive scan of one value per thread (blockDim.x <= 1024).
@@ -572,10 +720,10 @@ __device__ unsigned block_sum(unsigned x) {
 // every live vertex re-checks its support position, joins the bulk supporting
 // set of the support it keeps (a counting sort by support: count, grid-wide
 // scan, scatter), or is removed. Three internal grid barriers.
-__device__ bool ac6_entry(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint32_t nwarps,
+__device__ bool ac6_entry(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, uint32_t nwarps,
                           Counters& K) {
   const unsigned lane = lane_id();
-  const uint32_t r = R.round, n = D.n;
+  const uint32_t r = S.round, n = D.n;
   for (uint32_t base = gwarp * 32; base < n; base += nwarps * 32) {
     const uint32_t v = base + lane;
     const bool has = v < n;
@@ -598,9 +746,9 @@ __device__ bool ac6_entry(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint
       atomicAdd(&D.s_cnt[t], 1u);
     }
     K.swept += has ? 1 : 0;
-    append_dead(D, dies, v, r);
+    append_dead(D, B, dies, v, r, D.live0);
   }
-  if (!grid_sync(D, false)) return false;
+  if (!grid_barrier(D, B)) return false;
   // grid-wide exclusive scan of s_cnt into s_off
   const uint32_t chunk = ((n + gridDim.x - 1) / gridDim.x + 31) & ~31u;
   const uint32_t c0 = min(n, blockIdx.x * chunk), c1 = min(n, c0 + chunk);
@@ -610,7 +758,7 @@ __device__ bool ac6_entry(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint
     acc = block_sum(acc);
     if (threadIdx.x == 0) D.bsum[blockIdx.x] = acc;
   }
-  if (!grid_sync(D, false)) return false;
+  if (!grid_barrier(D, B)) return false;
   {
     unsigned pre = 0;
     for (uint32_t j = threadIdx.x; j < blockIdx.x; j += blockDim.x) pre += ldcg(&D.bsum[j]);
@@ -629,7 +777,7 @@ __device__ bool ac6_entry(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint
       D.s_off[n] = all;
     }
   }
-  if (!grid_sync(D, false)) return false;
+  if (!grid_barrier(D, B)) return false;
   for (uint32_t base = gwarp * 32; base < n; base += nwarps * 32) {
     const uint32_t v = base + lane;
     if (v < n && ldcg(&D.level[v]) == LIVE) {
@@ -643,18 +791,20 @@ __device__ bool ac6_entry(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint
   return true;
 }
 
-__device__ bool ac6_round(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint32_t nwarps,
+__device__ bool ac6_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, uint32_t nwarps,
                           Counters& K) {
-  if (R.prev_variant != TRIM_AC6_SUPPORT) return ac6_entry(D, R, gwarp, nwarps, K);
+  if (S.prev_variant != TRIM_AC6_SUPPORT) return ac6_entry(D, B, S, gwarp, nwarps, K);
   const unsigned lane = lane_id();
-  const uint32_t r = R.round;
-  const uint32_t N = R.fe - R.fb;
+  const uint32_t r = S.round;
+  const uint32_t N = S.fe - S.fb;
   const uint32_t G = min(32u, max(1u, (N + nwarps - 1) / nwarps));
-  for (uint32_t base = R.fb + gwarp * G; base < R.fe; base += nwarps * G) {
+  uint32_t* wb = B.wbuf[threadIdx.x >> 5];
+  for (uint32_t base = S.fb + gwarp * G; base < S.fe; base += nwarps * G) {
     const uint32_t item = base + lane;
-    const bool has = lane < G && item < R.fe;
+    const bool has = lane < G && item < S.fe;
     const uint32_t w = has ? ldcg(&D.log[item]) : 0u;
-    // bulk members of S(w): contiguous
+    uint32_t cur = has ? ldcg(&D.s_head[w]) : NIL;
+    // bulk members of S(w): contiguous, spread over the lanes
     uint32_t ss = 0, sd = 0;
     if (has) {
       ss = ldcg(&D.s_off[w]);
@@ -666,23 +816,41 @@ __device__ bool ac6_round(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint
     for (unsigned k0 = 0; k0 < total; k0 += 32) {
       const unsigned k = k0 + lane;
       const bool valid = k < total;
-      const unsigned j = owner_of(excl, k);
+      const unsigned j = G == 1 ? 0u : owner_of(excl, k);
       const unsigned sj = __shfl_sync(FULL, ss, j), ej = __shfl_sync(FULL, excl, j);
       const uint32_t v = valid ? ldcg(&D.s_list[sj + (k - ej)]) : 0u;
-      ac6_rescan(D, valid, v, r, K);
+      ac6_rescan(D, B, valid, v, r, K);
     }
-    // members that joined S(w) during the epoch: walk the lists, all lanes in step
-    uint32_t cur = has ? ldcg(&D.s_head[w]) : NIL;
-    uint32_t steps = 0;
-    while (__any_sync(FULL, cur != NIL)) {
-      if (++steps > D.n) {  // a set holds at most n members: a longer walk means a broken list
-        if (lane == 0) set_error(D, TRIM_ERR_STATE, 0xD4);
-        break;
+    // members that joined S(w) during the epoch (intrusive lists): all walkers
+    // hop in step and stage the members; re-scans run 32 at a time. A member's
+    // next pointer is read before it can be re-scanned (and move to another set).
+    unsigned nbuf = 0, steps = 0;
+    while (true) {
+      const bool walking = cur != NIL;
+      const unsigned wm = __ballot_sync(FULL, walking);
+      if (wm == 0u && nbuf == 0u) break;
+      if (wm) {
+        if (++steps > D.n) {  // a set holds at most n members: longer means a broken list
+          if (lane == 0) set_error(D, TRIM_ERR_STATE, 0xD4);
+          break;
+        }
+        if (walking) {
+          const uint32_t v = cur;
+          cur = ldcg(&D.s_next[v]);
+          wb[nbuf + __popc(wm & ((1u << lane) - 1u))] = v;
+        }
+        nbuf += __popc(wm);
+        __syncwarp();
       }
-      const bool valid = cur != NIL;
-      const uint32_t v = cur;
-      if (valid) cur = ldcg(&D.s_next[v]);  // read before v can move to another set
-      ac6_rescan(D, valid, v, r, K);
+      const bool more = __any_sync(FULL, cur != NIL);
+      while (nbuf >= 32u || (!more && nbuf > 0u)) {
+        const unsigned take = min(32u, nbuf);
+        const bool valid = lane < take;
+        const uint32_t v = valid ? wb[nbuf - take + lane] : 0u;
+        __syncwarp();
+        nbuf -= take;
+        ac6_rescan(D, B, valid, v, r, K);
+      }
     }
   }
   return true;
@@ -690,7 +858,7 @@ __device__ bool ac6_round(const Dev& D, const RoundInfo& R, uint32_t gwarp, uint
 
 // ------------------------------------------------------------------ init (round 0)
 
-__device__ void init_round(const Dev& D, uint32_t gwarp, uint32_t nwarps) {
+__device__ void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32_t nwarps) {
   const unsigned lane = lane_id();
   const uint32_t n = D.n;
   const bool w4 = (D.flags & F_AC4_POSSIBLE) != 0;
@@ -705,47 +873,56 @@ __device__ void init_round(const Dev& D, uint32_t gwarp, uint32_t nwarps) {
       if (w4) D.cnt[v] = d;
       if (w6) D.supp[v] = 0u;
     }
-    append_dead(D, has && d == 0u, v, 0u);
+    append_dead(D, B, has && d == 0u, v, 0u, D.live0, true);
   }
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(512, 2) trim_persistent_kernel(Dev D) {
-  __shared__ RoundInfo sR;
+__global__ void __launch_bounds__(512, 2) TRIM_KERNEL(Dev D) {
+  __shared__ Cta B;
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t nwarps = gridDim.x * wpb;
   const uint32_t gwarp = blockIdx.x * wpb + (threadIdx.x >> 5);
+  if (threadIdx.x == 0) {
+    Sched& S = B.S;
+    S.round = 0; S.fb = 0; S.fe = 0;
+    S.variant = NIL; S.prev_variant = NIL;
+    S.c4w = 0; S.e_c4 = 0; S.w_end = 0; S.e_end = 0;
+    S.ac3_list = NIL; S.live_in_len = 0; S.live_out = 0;
+    S.done = 0; S.fprev = 0;
+    S.m_live = D.m;
+    for (int i = 0; i < NFEAT; ++i) S.feat[i] = 0.0f;
+    for (int w = 0; w < MAX_WARPS; ++w) {
+      WarpSlice& x = B.ws[w];
+      x.nlog = x.nw4 = x.nedge = x.nlive = 0;
+      x.sum_in = x.sum_out = 0;
+      x.hist[0] = x.hist[1] = x.hist[2] = 0;
+    }
+    B.epoch = 0;
+    B.err = 0;
+  }
+  __syncthreads();
   Counters K;
-  init_round(D, gwarp, nwarps);
-  bool ok = grid_sync(D, true);
+  start_round(D, 0);
+  init_round(D, B, gwarp, nwarps);
+  flush_round(D, B, 0, D.live0);
+  bool ok = grid_barrier(D, B);
   while (ok) {
-    if (threadIdx.x == 0) {
-      const Ctrl* C = D.C;
-      sR.done = ld_relaxed(&C->done);
-      sR.round = ld_relaxed(&C->round);
-      sR.fb = ld_relaxed(&C->f_begin);
-      sR.fe = ld_relaxed(&C->f_end);
-      sR.variant = ld_relaxed(&C->variant);
-      sR.prev_variant = ld_relaxed(&C->prev_variant);
-      sR.c4 = ld_relaxed(&C->c4);
-      sR.ac3_list = ld_relaxed(&C->ac3_list);
-      sR.live_fill = ld_relaxed(&C->live_fill);
-      sR.npieces_prev = ld_relaxed(&C->rs[(sR.round - 1) & 3].npieces);
-      sR.live_in_len = sR.ac3_list == NIL ? 0u : ld_relaxed(&C->live_len[sR.ac3_list]);
-    }
+    if (threadIdx.x < 32) advance(D, B);
     __syncthreads();
-    const RoundInfo R = sR;
-    __syncthreads();
-    if (R.done) break;
-    if (R.variant == TRIM_AC4_PUSH) {
-      ac4_round(D, R, gwarp, nwarps, K);
-    } else if (R.variant == TRIM_AC6_SUPPORT) {
-      if (!ac6_round(D, R, gwarp, nwarps, K)) break;
-    } else {
-      ac3_round(D, R, gwarp, nwarps, K);
+    const Sched& S = B.S;  // changes only in advance(), between barriers
+    if (S.done) break;
+    start_round(D, S.round);
+    if ((MODES & M_AC4) && S.variant == TRIM_AC4_PUSH) {
+      ac4_round(D, B, S, gwarp, nwarps, K);
+    } else if ((MODES & M_AC6) && S.variant == TRIM_AC6_SUPPORT) {
+      if (!ac6_round(D, B, S, gwarp, nwarps, K)) break;
+    } else if (MODES & M_AC3) {
+      ac3_round(D, B, S, gwarp, nwarps, K);
     }
-    ok = grid_sync(D, true);
+    flush_round(D, B, S.round, S.live_out ? D.live1 : D.live0);
+    ok = grid_barrier(D, B);
   }
   if (D.flags & F_STATS) {
     const unsigned long long e = warp_sum(K.edges), p = warp_sum(K.pushed),
@@ -761,97 +938,3 @@ __global__ void __launch_bounds__(512, 2) trim_persistent_kernel(Dev D) {
 
 // ---------------------------------------------------------------- helpers
 
-// Control block reset before every run (one thread).
-__global__ void trim_reset_ctrl_kernel(Ctrl* C, uint64_t m) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    unsigned* w = reinterpret_cast<unsigned*>(C);
-    for (size_t i = 0; i < sizeof(Ctrl) / 4; ++i) w[i] = 0u;
-    C->prev_variant = NIL;
-    C->variant = NIL;
-    C->ac3_list = NIL;
-    C->m_live = m;
-    C->t_release = globaltimer();
-  }
-}
-
-__global__ void trim_status_kernel(const uint32_t* level, uint32_t n, uint8_t* status) {
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    status[v] = level[v] == LIVE ? 1 : 0;
-}
-
-// in-degree histogram of the targets (and a check that every target is < n)
-__global__ void trim_indeg_kernel(const uint32_t* tgt, uint64_t m, uint32_t n, uint32_t* cnt,
-                                  uint32_t* bad) {
-  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
-       e += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = tgt[e];
-    if (t < n) atomicAdd(&cnt[t], 1u);
-    else atomicOr(bad, 1u);
-  }
-}
-
-// exclusive scan, pass 1: each block scans `chunk` elements and writes its total
-__global__ void trim_scan_blocks_kernel(const uint32_t* in, uint32_t n, uint32_t* out,
-                                        uint32_t* block_sums, uint32_t chunk) {
-  const uint32_t c0 = min(n, blockIdx.x * chunk), c1 = min(n, c0 + chunk);
-  unsigned pre = 0;
-  for (uint32_t t0 = c0; t0 < c1; t0 += blockDim.x) {
-    const uint32_t i = t0 + threadIdx.x;
-    const unsigned x = i < c1 ? in[i] : 0u;
-    unsigned tot;
-    const unsigned ex = block_excl_scan(x, &tot);
-    if (i < c1) out[i] = pre + ex;
-    pre += tot;
-  }
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = pre;
-}
-
-// exclusive scan, pass 2: add the prefix of the block totals; out[n] = total
-__global__ void trim_scan_apply_kernel(uint32_t* out, uint32_t n, const uint32_t* block_sums,
-                                       uint32_t nblocks, uint32_t chunk) {
-  unsigned pre = 0;
-  for (uint32_t j = threadIdx.x; j < blockIdx.x; j += blockDim.x) pre += block_sums[j];
-  pre = block_sum(pre);
-  const uint32_t c0 = min(n, blockIdx.x * chunk), c1 = min(n, c0 + chunk);
-  for (uint32_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) out[i] += pre;
-  if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) {
-    unsigned all = 0;
-    for (uint32_t j = 0; j < nblocks; ++j) all += block_sums[j];
-    out[n] = all;
-  }
-}
-
-// G^T fill: predecessor u of t goes to itgt[ioff[t] + fill[t]++]
-__global__ void trim_transpose_fill_kernel(const uint32_t* off, const uint32_t* tgt, uint32_t n,
-                                           const uint32_t* ioff, uint32_t* fill, uint32_t* itgt) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t u = warp; u < n; u += nw) {
-    const uint32_t s = off[u], e = off[u + 1];
-    for (uint32_t k = s + lane; k < e; k += 32) {
-      const uint32_t t = tgt[k];
-      itgt[ioff[t] + atomicAdd(&fill[t], 1u)] = u;
-    }
-  }
-}
-
-// offsets: off[0] = 0, non-decreasing, off[n] = m
-__global__ void trim_validate_offsets_kernel(const uint32_t* off, uint32_t n, uint64_t m,
-                                             uint32_t* bad) {
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
-    if (v == 0 && off[0] != 0u) atomicOr(bad, 2u);
-    if (v == n && (uint64_t)off[n] != m) atomicOr(bad, 2u);
-    if (v < n && off[v + 1] < off[v]) atomicOr(bad, 2u);
-  }
-}
-
-// batched graphs: every edge stays inside its graph (vgraph[v] = graph id of v)
-__global__ void trim_validate_batch_kernel(const uint32_t* off, const uint32_t* tgt, uint32_t n,
-                                           const uint32_t* vgraph, uint32_t* bad) {
-  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-    const uint32_t g = vgraph[u];
-    for (uint32_t k = off[u]; k < off[u + 1]; ++k)
-      if (vgraph[tgt[k]] != g) atomicOr(bad, 4u);
-  }
-}

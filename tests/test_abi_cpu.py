@@ -42,7 +42,7 @@ def test_binding_declares_every_header_symbol(lib):
 def test_struct_layouts_match_header(lib):
     from paper_2107_12720_gb300.abi import TrimCsr, TrimParams, TrimRoundRec, TrimRunStats
     assert ctypes.sizeof(TrimCsr) == 40
-    assert ctypes.sizeof(TrimParams) == 40
+    assert ctypes.sizeof(TrimParams) == 32
     assert ctypes.sizeof(TrimRunStats) == 64
     assert ctypes.sizeof(TrimRoundRec) == 80
 
