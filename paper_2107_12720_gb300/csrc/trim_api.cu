@@ -51,6 +51,7 @@ struct trim_ctx {
   uint8_t* status_tmp = nullptr;
   trim_params_t params{};
   int grids[4] = {0, 0, 0, 0};
+  int last_flavour = 3;
   bool ran = false;
   bool pending = false;
   bool s_cnt_dirty = false;
@@ -361,7 +362,7 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
     default:
       ac4 = c->ioff != nullptr;
       ac6 = ac3 = true;
-      f |= trimk::F_NEED_FEATURES;
+      if (variant == TRIM_SCHED_LEARNED) f |= trimk::F_NEED_FEATURES;
   }
   if (c->flags & TRIM_FLAG_ROUND_LOG) f |= trimk::F_NEED_FEATURES;
   if (variant == TRIM_SCHED_SCRIPTED) {
@@ -411,6 +412,7 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
   // the lean single-variant flavours unless features or a per-round schedule are needed
   int flavour = 3;
   if (!(f & trimk::F_NEED_FEATURES) && variant <= TRIM_AC3_PULL) flavour = (int)variant;
+  c->last_flavour = flavour;
   const int grid = c->grids[flavour];
   if ((uint32_t)grid > 8192) return fail(c, TRIM_ERR_INVALID_ARG, "grid too large");
   trim_reset_ctrl_kernel<<<1, 32, 0, c->stream>>>(c->ctrl);

@@ -63,10 +63,10 @@ struct Counters {
 constexpr uint32_t LW = 256;  // entries per warp slice (per buffer)
 struct WarpSlice {
   uint32_t nlog, nw4, nedge, nlive;   // entries in the slices; edges of the w4 entries
+  uint32_t ncount;                    // removals counted in the log but not written to it
   uint32_t log_base, w4_base, edge_base, live_base;  // global bases at the CTA flush
   unsigned long long sum_in, sum_out;
   uint32_t hist[3];
-  uint32_t pad;
 };
 
 // Per-CTA shared state.
@@ -130,9 +130,9 @@ __device__ __noinline__ void warp_flush(const Dev& D, Cta& B, uint32_t r, uint32
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   WarpSlice& w = B.ws[warp];
   if (lane == 0) {
-    if (w.nlog) {
-      w.log_base = atomicAdd(&D.C->log_len, w.nlog);
-      if (w.log_base + w.nlog > D.n) { set_error(D, TRIM_ERR_STATE, 0xD1); w.nlog = 0; }
+    if (w.nlog + w.ncount) {
+      w.log_base = atomicAdd(&D.C->log_len, w.nlog + w.ncount);
+      if (w.log_base + w.nlog + w.ncount > D.n) { set_error(D, TRIM_ERR_STATE, 0xD1); w.nlog = 0; }
     }
     if (w.nw4) {
       const unsigned long long o = atomicAdd(
@@ -149,7 +149,7 @@ __device__ __noinline__ void warp_flush(const Dev& D, Cta& B, uint32_t r, uint32
   const WarpSlice c = w;
   copy_slices(D, c, warp, live_out);
   __syncwarp();
-  if (lane == 0) w.nlog = w.nw4 = w.nedge = w.nlive = 0;
+  if (lane == 0) w.nlog = w.nw4 = w.nedge = w.nlive = w.ncount = 0;
   __syncwarp();
 }
 
@@ -158,7 +158,7 @@ __device__ __noinline__ void warp_flush(const Dev& D, Cta& B, uint32_t r, uint32
 // joins the AC-4 work list with its G^T row and in-degree.
 __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uint32_t u,
                                             uint32_t r, uint32_t* live_out,
-                                            bool level_set = false) {
+                                            bool initial = false) {
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned mask = __ballot_sync(FULL, pred);
   if (mask == 0u) return;
@@ -177,11 +177,12 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   const unsigned eincl = warp_incl_scan(ew);
   const unsigned esum = __shfl_sync(FULL, eincl, 31);
   WarpSlice& ws = B.ws[warp];
-  if (ws.nlog + k > LW || ws.nw4 + kw > LW) warp_flush(D, B, r, live_out);
+  const unsigned kl = initial ? 0u : k;  // F_0 is only counted: no variant reads it back
+  if (ws.nlog + kl > LW || ws.nw4 + kw > LW) warp_flush(D, B, r, live_out);
   const uint32_t pl = ws.nlog, pw = ws.nw4, pe = ws.nedge;
-  if (pred) {
+  if (pred && !initial) {
     slice(warp, 0)[pl + __popc(mask & lt)] = u;
-    if (!level_set) D.level[u] = r;
+    D.level[u] = r;
   }
   if (w) {
     const unsigned at = pw + __popc(wmask & lt);
@@ -200,7 +201,8 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   }
   __syncwarp();
   if (lane == 0) {
-    ws.nlog = pl + k;
+    ws.nlog = pl + kl;
+    ws.ncount += k - kl;
     ws.nw4 = pw + kw;
     ws.nedge = pe + esum;
     if (feats) {
@@ -238,7 +240,8 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
   if (warp == 0) {
     // exclusive prefix of the per-warp counts (lane i holds warp i)
     const bool has = lane < nw;
-    const uint32_t a = has ? B.ws[lane].nlog : 0u, b = has ? B.ws[lane].nw4 : 0u,
+    const uint32_t a = has ? B.ws[lane].nlog + B.ws[lane].ncount : 0u,
+                   b = has ? B.ws[lane].nw4 : 0u,
                    c = has ? B.ws[lane].nedge : 0u, d = has ? B.ws[lane].nlive : 0u;
     const uint32_t ia = warp_incl_scan(a), ib = warp_incl_scan(b), ic = warp_incl_scan(c),
                    id = warp_incl_scan(d);
@@ -292,7 +295,7 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
   __syncwarp();
   if (lane == 0) {
     WarpSlice& w = B.ws[warp];
-    w.nlog = w.nw4 = w.nedge = w.nlive = 0;
+    w.nlog = w.nw4 = w.nedge = w.nlive = w.ncount = 0;
     w.sum_in = w.sum_out = 0;
     w.hist[0] = w.hist[1] = w.hist[2] = 0;
   }
@@ -392,20 +395,29 @@ __device__ __forceinline__ unsigned owner_of(unsigned excl, unsigned k) {
 
 __device__ __forceinline__ float log2p1(float x) { return log2f(1.0f + x); }
 
-// Cost rule of TRIM_SCHED_HEURISTIC (work each variant would do next round, in
-// rough units of one random 32-byte access): AC-4 walks the in-edges of every
-// removed vertex it has not yet processed; AC-3 sweeps its live list (or all n
-// the first time); AC-6 re-scans the supporting sets of the last frontier
-// (about one member per removed vertex) or, on entry, rebuilds the sets of all
-// live vertices.
+// Cost rule of TRIM_SCHED_HEURISTIC: the work each variant would do in round
+// r+1, in units of one random memory access, with one-time entry costs spread
+// over a horizon of H rounds (a greedy rule that charged them to one round
+// would never leave a variant whose cost recurs every round).
+//   AC-4: pushes every in-edge of the removed vertices it has not processed yet
+//         (the backlog beyond the newest frontier is a one-time cost).
+//   AC-3: sweeps its live list (all n vertices the first time), every round.
+//   AC-6: while it runs, re-scans about one supporting-set member per removed
+//         vertex; entering it rebuilds the sets of all live vertices.
 __device__ uint32_t heuristic_choice(const Dev& D, const Sched& L, uint32_t nF, uint32_t n_live,
                                      uint32_t w_end, uint32_t e_end) {
+  constexpr float H = 4.0f;
   const float inf = 3.0e38f;
-  float c4 = (float)(e_end - L.e_c4) + 0.5f * (float)(w_end - L.c4w);
+  const float eF = (float)(e_end - L.e_end);          // in-edges of the newest frontier
+  const float backlog = (float)(e_end - L.e_c4);      // in-edges not yet pushed
+  const float items = (float)(w_end - L.c4w);
+  float c4 = (L.variant == TRIM_AC4_PUSH) ? eF + 0.25f * items
+                                           : (backlog - eF) / H + eF + 0.25f * items;
   const float sweep = (L.ac3_list == NIL) ? (float)D.n : (float)L.live_in_len;
-  float c3 = 0.35f * sweep + 0.5f * (float)nF;
-  float c6 = (L.variant == TRIM_AC6_SUPPORT) ? 2.0f * (float)nF
-                                             : 1.5f * (float)n_live + 0.25f * (float)D.n;
+  float c3 = 2.0f * sweep;
+  float c6 = (L.variant == TRIM_AC6_SUPPORT)
+                 ? 4.0f * (float)nF
+                 : (3.0f * (float)n_live + (float)D.n) / H + 4.0f * (float)nF;
   c4 *= D.heur_push_ratio;
   c6 *= D.heur_ac6_ratio;
   if (!(D.flags & F_AC4_POSSIBLE) || D.ioff == nullptr) c4 = inf;
@@ -895,7 +907,7 @@ __global__ void __launch_bounds__(512, 2) TRIM_KERNEL(Dev D) {
     for (int i = 0; i < NFEAT; ++i) S.feat[i] = 0.0f;
     for (int w = 0; w < MAX_WARPS; ++w) {
       WarpSlice& x = B.ws[w];
-      x.nlog = x.nw4 = x.nedge = x.nlive = 0;
+      x.nlog = x.nw4 = x.nedge = x.nlive = x.ncount = 0;
       x.sum_in = x.sum_out = 0;
       x.hist[0] = x.hist[1] = x.hist[2] = 0;
     }
