@@ -223,6 +223,41 @@ trim_err_t trim_mlp_loss_grad(const float* params, const float* X, const uint8_t
 trim_err_t trim_mlp_adam_step(float* params, const float* grad, float* m, float* v, uint32_t t,
                               float lr, float beta1, float beta2, float eps, void* cuda_stream);
 
+/* ---- Trimming without any device allocation (no counterpart in the paper) ----
+ * For callers that cannot call cudaMalloc when they need a result: processes
+ * under an allocator discipline that forbids new device allocations, plugins
+ * that must not touch the host application's allocator, or paths that must
+ * not synchronise the device the way cudaMalloc/cudaFree can.
+ *
+ * trim_run_ac4_noalloc runs the same AC-4 kernel as trim_run(TRIM_AC4_PUSH) and
+ * writes the same levels, but takes all its scratch (counters, dead log, AC-4
+ * work list, control block) from one fixed __device__ array compiled into the
+ * library: TRIM_NOALLOC_SCRATCH_BYTES per GPU, held by every GPU that loads the
+ * library until the process exits. Nothing is allocated per call.
+ *
+ * All pointers are DEVICE pointers supplied by the caller: the graph in CSR
+ * (offsets n+1, targets m), its transpose G^T (in_offsets n+1, in_targets m;
+ * the caller builds it, e.g. once with trim_create + a trim_run of AC-4 on a
+ * context, or on its own), and level_out (n uint32: levels as trim_level,
+ * TRIM_LIVE for survivors). rounds_out (host, nullable) receives alpha.
+ * Sizes above TRIM_NOALLOC_MAX_N vertices or TRIM_NOALLOC_MAX_M edges are
+ * rejected with TRIM_ERR_TOO_LARGE before any device work.
+ *
+ * The first call on each device (with that device current) looks up the
+ * array's device address and the launch shape; make that first call before
+ * any stream capture. Every call on a device uses the same array, which keeps
+ * the previous call's contents (the call clears what must start at zero):
+ * calls whose GPU work overlaps (several streams, several host threads) race
+ * on it and must be serialised by the caller. The call waits for its work on
+ * cuda_stream before it returns, to report device-side errors. */
+#define TRIM_NOALLOC_MAX_N (1u << 18)
+#define TRIM_NOALLOC_MAX_M (1u << 22)
+#define TRIM_NOALLOC_SCRATCH_BYTES 5768960u
+trim_err_t trim_run_ac4_noalloc(const uint32_t* offsets, const uint32_t* targets,
+                                const uint32_t* in_offsets, const uint32_t* in_targets,
+                                uint32_t n, uint32_t m, uint32_t* level_out,
+                                uint32_t* rounds_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,7 @@ SIGNATURES = [
     ("trim_mlp_forward", _I, [_P, _P, _U32, _P, _P]),
     ("trim_mlp_loss_grad", _I, [_P, _P, _P, _U32, _P, _P, _P, _P]),
     ("trim_mlp_adam_step", _I, [_P, _P, _P, _P, _U32, _F, _F, _F, _F, _P]),
+    ("trim_run_ac4_noalloc", _I, [_P, _P, _P, _P, _U32, _U32, _P, ctypes.POINTER(_U32), _P]),
 ]
 
 _lib = None
@@ -232,3 +233,20 @@ def trim_mlp_adam_step(params, grad, m, v, t: int, lr: float, beta1: float, beta
                        eps: float, stream) -> None:
     check(lib().trim_mlp_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), t, lr, beta1,
                                    beta2, eps, stream))
+
+
+TRIM_NOALLOC_MAX_N = 1 << 18
+TRIM_NOALLOC_MAX_M = 1 << 22
+
+
+def trim_run_ac4_noalloc(offsets, targets, in_offsets, in_targets, n: int, m: int, level_out,
+                         stream) -> int:
+    """AC-4 trimming with the library's fixed scratch array (no device allocation);
+    all arrays are device tensors/pointers. Returns alpha."""
+    rounds = ctypes.c_uint32(0)
+    rc = lib().trim_run_ac4_noalloc(_ptr(offsets), _ptr(targets), _ptr(in_offsets),
+                                    _ptr(in_targets), n, m, _ptr(level_out),
+                                    ctypes.byref(rounds), stream)
+    if rc != 0:
+        raise TrimError(rc, "trim_run_ac4_noalloc failed")
+    return int(rounds.value)

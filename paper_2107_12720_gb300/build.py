@@ -24,6 +24,7 @@ UNITS = [("trim_kernels.cu", ["-DTRIM_MODES=1"], "trim_kernels_m1.o"),
          ("trim_kernels.cu", ["-DTRIM_MODES=15"], "trim_kernels_m15.o"),
          ("trim_aux.cu", [], "trim_aux.o"),
          ("trim_api.cu", [], "trim_api.o"),
+         ("trim_noalloc.cu", [], "trim_noalloc.o"),
          ("mlp.cu", [], "mlp.o")]
 SOURCES = sorted({u[0] for u in UNITS})
 HEADERS = ["trim_internal.cuh", os.path.join("..", "..", "include", "trim.h")]
