@@ -265,11 +265,15 @@ def run_reference(args, rank, ws):
 
 # ---------------------------------------------------------------- GPU arm
 
-def time_variant(P, t, variant, steps, warmup, flush_buf):
+def time_variant(P, t, variant, steps, warmup, flush_buf, graph_off=None):
+    """Device time of `steps` complete trims (L2 flushed before each). With
+    graph_off the step is one batched trim (trim_batch_run, a replayed CUDA
+    graph) of all packed graphs."""
     import torch
     stream = t.stream
+    run = (lambda: t.batch_run(graph_off, variant)) if graph_off is not None else None
     for _ in range(warmup):
-        t.run(variant)
+        run() if run else t.run(variant)
     times, kern = [], []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -277,15 +281,40 @@ def time_variant(P, t, variant, steps, warmup, flush_buf):
     for _ in range(steps):
         flush_buf.add_(1)  # writes more than the L2 holds, on the same stream
         e0.record(stream)
-        t.run_async(variant)
-        e1.record(stream)
-        last = t.sync()
+        if run:
+            last = run()
+            e1.record(stream)
+        else:
+            t.run_async(variant)
+            e1.record(stream)
+            last = t.sync()
+        e1.synchronize()
         times.append(e0.elapsed_time(e1))
         kern.append(last["device_ms"])
     return times, kern, last
 
 
-def e2e_measure(P, g, off_in, tgt_in, variant, steps):
+def per_graph_fixed(P, g, variant="ac4", limit=None):
+    """The unbatched schedule: every packed graph trimmed alone with one fixed
+    variant (one context per graph, G^T given); returns the summed device time
+    (context creation and copies excluded) and the graphs timed."""
+    go = g.graph_off.astype(np.int64)
+    total_ms, count = 0.0, 0
+    idx = range(len(go) - 1) if limit is None else range(0, len(go) - 1, max(1, (len(go) - 1) // limit))
+    for gi in idx:
+        a, b = int(go[gi]), int(go[gi + 1])
+        off = (g.off[a:b + 1] - g.off[a]).astype(np.uint32)
+        tgt = (g.tgt[g.off[a]:g.off[b]] - a).astype(np.uint32)
+        oi, ti = host_transpose(off, tgt)
+        with P.Trimmer(off, tgt, oi, ti) as t:
+            t.run(variant)
+            total_ms += t.run(variant)["device_ms"]
+        count += 1
+    scale = (len(go) - 1) / count
+    return total_ms * scale, count
+
+
+def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None):
     """Through the C ABI with host buffers: trim_create copies the pinned host
     CSR (and G^T) to the device, trim_run trims, trim_level copies the levels
     back; all inside the host wall-clock timing."""
@@ -298,7 +327,7 @@ def e2e_measure(P, g, off_in, tgt_in, variant, steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with P.Trimmer(ho, ht, hoi, hti) as t:
-            t.run(variant)
+            t.batch_run(graph_off, variant) if graph_off is not None else t.run(variant)
             P.trim_level(t.ctx, out.data_ptr(), 0)
         t1 = time.perf_counter()
         if s:  # the first call pays one-time costs (module load, context)
@@ -323,11 +352,13 @@ def run_ours(args, rank, ws, local):
     if have_model:
         t.set_model(np.load(model))
     headline = args.variant or ("learned" if have_model else "heuristic")
+    batched = g.graph_off is not None
+    gofs = g.graph_off if batched else None
 
     sweep = {}
     if args.sweep and rank == 0:
         for v in ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if have_model else []):
-            ts, ks, st = time_variant(P, t, v, max(20, args.steps // 10), 3, flush)
+            ts, ks, st = time_variant(P, t, v, max(20, args.steps // 10), 3, flush, gofs)
             sweep[v] = {"ms": statistics.mean(ts), "kernel_ms": statistics.mean(ks),
                         "edges_per_s": g.m / (statistics.mean(ts) * 1e-3),
                         "rounds_by_variant": st["rounds_by_variant"]}
@@ -339,10 +370,10 @@ def run_ours(args, rank, ws, local):
     if rank == 0:
         clocks.start()
     for _ in range(args.warmup):
-        t.run(headline)
+        t.batch_run(gofs, headline) if batched else t.run(headline)
     barrier(ws)
     torch.cuda.synchronize()
-    ts, ks, st = time_variant(P, t, headline, args.steps, 0, flush)
+    ts, ks, st = time_variant(P, t, headline, args.steps, 0, flush, gofs)
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop() if rank == 0 else None
@@ -354,7 +385,7 @@ def run_ours(args, rank, ws, local):
 
     e2e = None
     if rank == 0 and args.e2e_steps > 0:
-        ev, h2d, d2h = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps)
+        ev, h2d, d2h = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs)
         e2e = {"value": ev * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
     t.close()
@@ -383,6 +414,16 @@ def run_ours(args, rank, ws, local):
     }
     if sweep:
         line["variants"] = sweep
+    if batched:
+        line["config"]["graphs"] = int(len(g.graph_off) - 1)
+        line["config"]["timing"] = ("CUDA events around trim_batch_run: one replayed CUDA graph "
+                                    "(control-block reset + persistent kernel) for all graphs")
+        if args.per_graph:
+            ms, cnt = per_graph_fixed(P, g, "ac4", None if args.per_graph <= 0 else args.per_graph)
+            line["per_graph_fixed"] = {"schedule": "ac4, each graph trimmed alone", "ms": ms,
+                                       "value": g.m / (ms * 1e-3), "unit": UNIT,
+                                       "graphs_timed": cnt,
+                                       "batched_speedup": ms / (step_s * 1e3)}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -400,6 +441,9 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-graph", type=int, default=0,
+                    help="batched workload: also time each graph alone (N>0: a sample of N graphs, "
+                         "-1: all)")
     args = ap.parse_args(argv)
     rank, ws, local = dist_setup()
     if args.impl == "reference":

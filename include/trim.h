@@ -120,6 +120,8 @@ typedef struct {
   uint32_t removed;      /* |F_r|                                                     */
   uint64_t t_start_ns;   /* device %globaltimer at the start of the round              */
   uint64_t t_end_ns;     /* ... at its end (after the grid-wide barrier)               */
+  uint64_t t_work_ns;    /* ... when the first CTA finished its share of the work     */
+  uint64_t t_flush_ns;   /* ... when the first CTA finished moving its buffers out    */
   float features[12];
 } trim_round_rec_t;
 

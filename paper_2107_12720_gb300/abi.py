@@ -55,6 +55,7 @@ class TrimRoundRec(ctypes.Structure):
     _fields_ = [("round", ctypes.c_uint32), ("variant", ctypes.c_uint32),
                 ("frontier", ctypes.c_uint32), ("removed", ctypes.c_uint32),
                 ("t_start_ns", ctypes.c_uint64), ("t_end_ns", ctypes.c_uint64),
+                ("t_work_ns", ctypes.c_uint64), ("t_flush_ns", ctypes.c_uint64),
                 ("features", ctypes.c_float * 12)]
 
 

@@ -52,6 +52,11 @@ struct trim_ctx {
   trim_params_t params{};
   int grids[4] = {0, 0, 0, 0};
   int last_flavour = 3;
+  cudaGraphExec_t batch_exec = nullptr;  // captured batched launch (trim_batch_run)
+  cudaStream_t cap_stream = nullptr;      // private stream used only for that capture
+  bool capturing = false;
+  int batch_variant = -1;
+  uint64_t batch_graph_launches = 0;
   bool ran = false;
   bool pending = false;
   bool s_cnt_dirty = false;
@@ -105,7 +110,9 @@ trim_err_t dalloc(trim_ctx* c, T** p, size_t count) {
 
 void release(trim_ctx* c) {
   if (!c) return;
-  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->stream);
+  if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void* p : c->owned) cudaFree(p);
   c->owned.clear();
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
@@ -364,7 +371,9 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
       ac6 = ac3 = true;
       if (variant == TRIM_SCHED_LEARNED) f |= trimk::F_NEED_FEATURES;
   }
-  if (c->flags & TRIM_FLAG_ROUND_LOG) f |= trimk::F_NEED_FEATURES;
+  // scheduler features: for the learned scheduler, and in round logs of scheduled runs
+  if ((c->flags & TRIM_FLAG_ROUND_LOG) && variant >= TRIM_SCHED_HEURISTIC)
+    f |= trimk::F_NEED_FEATURES;
   if (variant == TRIM_SCHED_SCRIPTED) {
     std::vector<uint8_t> s(c->script_len);
     CK(cudaMemcpy(s.data(), c->script, c->script_len, cudaMemcpyDeviceToHost));
@@ -411,18 +420,21 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
   D.heur_ac6_ratio = c->params.heur_ac6_ratio;
   // the lean single-variant flavours unless features or a per-round schedule are needed
   int flavour = 3;
-  if (!(f & trimk::F_NEED_FEATURES) && variant <= TRIM_AC3_PULL) flavour = (int)variant;
+  if (variant <= TRIM_AC3_PULL) flavour = (int)variant;
   c->last_flavour = flavour;
   const int grid = c->grids[flavour];
   if ((uint32_t)grid > 8192) return fail(c, TRIM_ERR_INVALID_ARG, "grid too large");
   trim_reset_ctrl_kernel<<<1, 32, 0, c->stream>>>(c->ctrl);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(c->ev0, c->stream));  // device_ms covers the persistent kernel alone
+  // device_ms covers the persistent kernel alone; inside a stream capture the
+  // records must be "external" to become event-record nodes of the graph
+  const unsigned rec = c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  CK(cudaEventRecordWithFlags(c->ev0, c->stream, rec));
   void* args[] = {&D};
   CK(cudaLaunchCooperativeKernel((const void*)kFlavours[flavour], dim3(grid),
                                  dim3(c->params.block_threads), args, dyn_smem_bytes(),
                                  c->stream));
-  CK(cudaEventRecord(c->ev1, c->stream));
+  CK(cudaEventRecordWithFlags(c->ev1, c->stream, rec));
   c->pending = true;
   c->last_mode = variant;
   c->ran = false;
@@ -483,12 +495,58 @@ trim_err_t validate_batch(trim_ctx* c, const uint32_t* graph_off, uint32_t G) {
 }
 
 // The packed CSR of independent graphs is itself one graph (their disjoint
-// union), whose levels equal those of each graph trimmed alone.
+// union), whose levels equal those of each graph trimmed alone. All graphs run
+// in one persistent launch, so every round's fixed cost (barrier, bookkeeping)
+// is shared by all graphs still peeling. The launch (control-block reset plus
+// persistent kernel) is captured once into a CUDA graph and replayed.
 trim_err_t enqueue_batch(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
                          trim_variant_t variant) {
   (void)graph_off;
   (void)G;
-  return enqueue_run(c, variant);
+  if (c->batch_exec == nullptr || c->batch_variant != (int)variant) {
+    // one direct run first: builds G^T if needed, sizes the work list, and
+    // leaves all allocations in place before the capture
+    TRY(enqueue_run(c, variant));
+    TRY(finish_run(c, nullptr));
+    if (c->batch_exec) {
+      cudaGraphExecDestroy(c->batch_exec);
+      c->batch_exec = nullptr;
+    }
+    // capture on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is then launched on c->stream
+    if (c->cap_stream == nullptr)
+      CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaStream_t user_stream = c->stream;
+    c->stream = c->cap_stream;
+    c->capturing = true;
+    cudaError_t be = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    trim_err_t e = be == cudaSuccess ? enqueue_run(c, variant) : TRIM_ERR_CUDA;
+    cudaError_t ce = be == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &graph) : be;
+    c->capturing = false;
+    c->stream = user_stream;
+    if (e != TRIM_OK || ce != cudaSuccess) {  // not capturable here: launch directly
+      if (graph) cudaGraphDestroy(graph);
+      (void)cudaGetLastError();
+      c->pending = false;
+      return enqueue_run(c, variant);
+    }
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      (void)cudaGetLastError();
+      c->pending = false;
+      return enqueue_run(c, variant);
+    }
+    c->batch_exec = exec;
+    c->batch_variant = (int)variant;
+  }
+  CK(cudaGraphLaunch(c->batch_exec, c->stream));
+  c->pending = true;
+  c->ran = false;
+  c->batch_graph_launches++;
+  return TRIM_OK;
 }
 
 }  // namespace
@@ -584,6 +642,16 @@ trim_err_t trim_default_params(trim_params_t* p) {
   return TRIM_OK;
 }
 
+// a captured batched launch embeds the kernel arguments: drop it when they change
+static void drop_batch_graph(trim_ctx* c) {
+  if (c && c->batch_exec) {
+    cudaStreamSynchronize(c->stream);
+    cudaGraphExecDestroy(c->batch_exec);
+    c->batch_exec = nullptr;
+    c->batch_variant = -1;
+  }
+}
+
 trim_err_t trim_set_params(trim_ctx* c, const trim_params_t* p) {
   if (!c || !p) return fail(c, TRIM_ERR_INVALID_ARG, "null argument");
   if (p->block_threads < 128 || p->block_threads > 512 || p->block_threads % 32)
@@ -591,6 +659,7 @@ trim_err_t trim_set_params(trim_ctx* c, const trim_params_t* p) {
   if (p->spin_limit_ns == 0) return fail(c, TRIM_ERR_INVALID_ARG, "spin_limit_ns must be > 0");
   if (!(p->heur_push_ratio > 0.0f) || !(p->heur_ac6_ratio > 0.0f))
     return fail(c, TRIM_ERR_INVALID_ARG, "heuristic ratios must be > 0");
+  drop_batch_graph(c);
   const trim_params_t old = c->params;
   c->params = *p;
   trim_err_t e = compute_grid(c);
@@ -611,11 +680,13 @@ trim_err_t trim_get_params(const trim_ctx* c, trim_params_t* p) {
 trim_err_t trim_set_model(trim_ctx* c, const float* blob, size_t n_floats) {
   if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
   if (blob == nullptr) {
+    drop_batch_graph(c);
     c->has_model = false;
     return TRIM_OK;
   }
   if (n_floats != TRIM_MLP_NBLOB)
     return fail(c, TRIM_ERR_INVALID_ARG, "model blob must hold TRIM_MLP_NBLOB floats");
+  drop_batch_graph(c);
   if (!c->model) TRY(dalloc(c, &c->model, TRIM_MLP_NBLOB));
   CK(cudaMemcpyAsync(c->model, blob, TRIM_MLP_NBLOB * 4, cudaMemcpyHostToDevice, c->stream));
   TRY(sync_check(c));
@@ -627,6 +698,7 @@ trim_err_t trim_set_schedule(trim_ctx* c, const uint8_t* v, uint32_t len) {
   if (!c || (!v && len)) return fail(c, TRIM_ERR_INVALID_ARG, "null argument");
   for (uint32_t i = 0; i < len; ++i)
     if (v[i] > 2) return fail(c, TRIM_ERR_INVALID_ARG, "schedule entries must be 0..2");
+  drop_batch_graph(c);
   if (len > c->script_len || !c->script) {
     uint8_t* s = nullptr;
     TRY(dalloc(c, &s, len));

@@ -50,6 +50,8 @@ struct Ctrl {
   unsigned int rlog_len;
   unsigned int _p3[27];
   unsigned long long t_round[4];  // CTA 0's %globaltimer at the start of round r (ring)
+  unsigned long long t_work[4];   // ... when CTA 0 finished the work of round r
+  unsigned long long t_flush[4];  // ... when CTA 0 finished flushing round r
   unsigned long long stats[4];    // edges inspected, in-edges pushed, candidates, live swept
   RoundStat rs[4];
 };
@@ -71,6 +73,7 @@ struct Sched {
   uint32_t live_out;      // output list of an AC-3 round
   uint32_t done;
   uint32_t fprev;         // frontier size of round r-1 (timing feature)
+  uint32_t mixed;         // 1 once a round ran AC-6 or AC-3 (AC-4 must then re-check levels)
   unsigned long long m_live;     // out-edges of live vertices
   float feat[12];                // features that chose this round's variant
 };

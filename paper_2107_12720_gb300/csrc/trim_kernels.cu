@@ -39,18 +39,31 @@
 #endif
 #define TRIM_CAT2(a, b) a##b
 #define TRIM_CAT(a, b) TRIM_CAT2(a, b)
+#ifdef TRIM_KERNEL_SUFFIX
+#define TRIM_KERNEL TRIM_CAT(trim_persistent_kernel_m, TRIM_KERNEL_SUFFIX)
+#else
 #define TRIM_KERNEL TRIM_CAT(trim_persistent_kernel_m, TRIM_MODES)
+#endif
 
 using namespace trimk;
 
 namespace {
 
 constexpr int MODES = TRIM_MODES;
+// In the all-variant flavour each round function keeps its own register
+// allocation, so the heavier AC-6 code cannot push the AC-4 loop into spills.
+#if TRIM_MODES == 15
+#define ROUND_FN __noinline__
+#else
+#define ROUND_FN __forceinline__
+#endif
 constexpr int M_AC4 = 1, M_AC6 = 2, M_AC3 = 4, M_SCHED = 8;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int MAX_WARPS = 16;   // blockDim.x <= 512
 constexpr int WBUF = 64;        // per-warp staging of supporting-set members
 
+// Work counters (TRIM_FLAG_STATS). Each round function keeps its own in
+// registers and adds them to the global totals when it returns.
 struct Counters {
   unsigned long long edges = 0, pushed = 0, cand = 0, swept = 0;
 };
@@ -71,6 +84,9 @@ struct WarpSlice {
 
 // Per-CTA shared state.
 struct Cta {
+#if TRIM_MODES & 8
+  float model[TRIM_MLP_NBLOB];  // scheduler MLP (copied once per launch)
+#endif
   Sched S;
   WarpSlice ws[MAX_WARPS];
   unsigned epoch;  // grid barriers passed
@@ -326,6 +342,19 @@ __device__ bool grid_barrier(const Dev& D, Cta& B) {
   return B.err == 0u;
 }
 
+// Warp-collective: adds this warp's counters to the run totals (stats runs only).
+__device__ __forceinline__ void stats_flush(const Dev& D, const Counters& K) {
+  if (!(D.flags & F_STATS)) return;
+  const unsigned long long e = warp_sum(K.edges), p = warp_sum(K.pushed), c = warp_sum(K.cand),
+                           s = warp_sum(K.swept);
+  if (lane_id() == 0) {
+    if (e) atomicAdd(&D.C->stats[0], e);
+    if (p) atomicAdd(&D.C->stats[1], p);
+    if (c) atomicAdd(&D.C->stats[2], c);
+    if (s) atomicAdd(&D.C->stats[3], s);
+  }
+}
+
 // ------------------------------------------------------------------ scans
 
 // Thread-level forward scan of v's successors from position i (row start s,
@@ -430,30 +459,33 @@ __device__ uint32_t heuristic_choice(const Dev& D, const Sched& L, uint32_t nF, 
 
 // Warp-collective MLP 12 -> 32 -> 32 -> 3 (ReLU); returns the argmax class
 // among the available variants; *in_range = all features inside [lo, hi].
-__device__ uint32_t mlp_choice(const Dev& D, const float* f, bool* in_range) {
+// Warp-collective MLP 12 -> 32 -> 32 -> 3 (ReLU) on the shared-memory copy of
+// the model (layers stored transposed so that lane j reads column j without bank
+// conflicts); returns the argmax class among the available variants and
+// whether every feature lies in the model's training range.
+__device__ uint32_t mlp_choice(const Dev& D, const float* B, const float* f, bool* in_range) {
   const unsigned lane = lane_id();
-  const float* B = D.model;
-  const float *W1 = B, *b1 = B + 384, *W2 = B + 416, *b2 = B + 1440, *W3 = B + 1472,
+  const float *W1t = B, *b1 = B + 384, *W2t = B + 416, *b2 = B + 1440, *W3 = B + 1472,
               *b3 = B + 1568, *mean = B + 1571, *istd = B + 1583, *lo = B + 1595,
               *hi = B + 1607;
   bool ok = true;
   float x[NFEAT];
 #pragma unroll
   for (int i = 0; i < NFEAT; ++i) {
-    ok = ok && f[i] >= __ldg(&lo[i]) && f[i] <= __ldg(&hi[i]);
-    x[i] = (f[i] - __ldg(&mean[i])) * __ldg(&istd[i]);
+    ok = ok && f[i] >= lo[i] && f[i] <= hi[i];
+    x[i] = (f[i] - mean[i]) * istd[i];
   }
-  float h1 = __ldg(&b1[lane]);
+  float h1 = b1[lane];
 #pragma unroll
-  for (int i = 0; i < NFEAT; ++i) h1 = fmaf(__ldg(&W1[lane * NFEAT + i]), x[i], h1);
+  for (int i = 0; i < NFEAT; ++i) h1 = fmaf(W1t[i * 32 + lane], x[i], h1);
   h1 = fmaxf(h1, 0.0f);
-  float h2 = __ldg(&b2[lane]);
+  float h2 = b2[lane];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) h2 = fmaf(__ldg(&W2[lane * 32 + k]), __shfl_sync(FULL, h1, k), h2);
+  for (int k = 0; k < 32; ++k) h2 = fmaf(W2t[k * 32 + lane], __shfl_sync(FULL, h1, k), h2);
   h2 = fmaxf(h2, 0.0f);
   float z[3];
 #pragma unroll
-  for (int o = 0; o < 3; ++o) z[o] = warp_sum(__ldg(&W3[o * 32 + lane]) * h2) + __ldg(&b3[o]);
+  for (int o = 0; o < 3; ++o) z[o] = warp_sum(W3[o * 32 + lane] * h2) + b3[o];
   if (D.ioff == nullptr || !(D.flags & F_AC4_POSSIBLE)) z[TRIM_AC4_PUSH] = -3.0e38f;
   if (!(D.flags & F_AC6_POSSIBLE)) z[TRIM_AC6_SUPPORT] = -3.0e38f;
   if (!(D.flags & F_AC3_POSSIBLE)) z[TRIM_AC3_PULL] = -3.0e38f;
@@ -468,7 +500,7 @@ __device__ uint32_t mlp_choice(const Dev& D, const float* f, bool* in_range) {
 // sink pass): closes round r in the CTA's copy of the schedule and prepares
 // round r+1. Reads only values that are final for every CTA at this point, so
 // all copies take the same decisions. CTA 0 also publishes results and logs.
-__device__ void advance(const Dev& D, Cta& B) {
+__device__ ROUND_FN void advance(const Dev& D, Cta& B) {
   const unsigned lane = lane_id();
   Ctrl* C = D.C;
   Sched L = B.S;
@@ -492,6 +524,8 @@ __device__ void advance(const Dev& D, Cta& B) {
         rec->removed = nF;
         rec->t_start_ns = ld_relaxed64(&C->t_round[r & 3]);
         rec->t_end_ns = globaltimer();
+        rec->t_work_ns = ld_relaxed64(&C->t_work[r & 3]);
+        rec->t_flush_ns = ld_relaxed64(&C->t_flush[r & 3]);
         for (int i = 0; i < NFEAT; ++i) rec->features[i] = L.feat[i];
         C->rlog_len = r;
       }
@@ -536,7 +570,7 @@ __device__ void advance(const Dev& D, Cta& B) {
       f[9] = (float)h2 / (float)nF;
       // time of round r-1 per vertex of its frontier (CTA 0's clock, published to all)
       f[10] = (r >= 2) ? log2p1((float)(t_r - t_rm1) / (float)max(1u, L.fprev)) : 0.0f;
-      f[11] = (float)(r + 1) / (float)(r + 1 + 64);
+      f[11] = (r >= 1) ? (float)L.variant : -1.0f;  // the variant whose state is current
     }
     uint32_t next;
     if (!(MODES & M_SCHED) || D.mode <= TRIM_AC3_PULL) {
@@ -549,13 +583,18 @@ __device__ void advance(const Dev& D, Cta& B) {
       next = heuristic_choice(D, L, nF, n_live, w_end, e_end);
       if (D.mode == TRIM_SCHED_LEARNED && D.model != nullptr) {
         bool in_range = false;
-        const uint32_t learned = mlp_choice(D, f, &in_range);
+#if TRIM_MODES & 8
+        const uint32_t learned = mlp_choice(D, B.model, f, &in_range);
+#else
+        const uint32_t learned = next;
+#endif
         if (in_range) next = learned;
       }
     }
     L.prev_variant = (r >= 1) ? L.variant : NIL;
     L.fprev = L.fe - L.fb;  // frontier of round r, for the timing feature two rounds on
     L.variant = next;
+    if (next != TRIM_AC4_PUSH) L.mixed = 1;
     L.round = r + 1;
     L.fb = L.fe;
     L.fe = len;
@@ -587,13 +626,14 @@ __device__ __forceinline__ void start_round(const Dev& D, uint32_t k) {
 // in-edges spread over many warps. The owner of a chunk's first edge comes from
 // chunk_first; the next 31 work-list entries own the rest of the chunk (every
 // entry has at least one edge), and a shuffle search finds each lane's owner.
-__device__ void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, uint32_t nwarps,
-                          Counters& K) {
+__device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp,
+                                   uint32_t nwarps) {
   constexpr int U = 4;  // chunks in flight per warp
+  Counters K;
   const unsigned lane = lane_id();
   const uint32_t r = S.round;
   // a vertex whose counter reaches zero is still live unless another variant ran
-  const bool check = D.mode != TRIM_AC4_PUSH;
+  const bool check = (MODES != M_AC4) && S.mixed;
   const uint32_t ea = S.e_c4, eb = S.e_end, ia = S.c4w, ib = S.w_end;
   if (eb <= ea) return;
   const uint32_t c0 = ea >> 5, c1 = (eb + 31u) >> 5;
@@ -629,12 +669,14 @@ __device__ void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, 
       append_dead(D, B, pred, u[q], r, D.live0);
     }
   }
+  stats_flush(D, K);
 }
 
 // ------------------------------------------------------------------ AC-3
 
-__device__ void ac3_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, uint32_t nwarps,
-                          Counters& K) {
+__device__ ROUND_FN void ac3_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp,
+                                   uint32_t nwarps) {
+  Counters K;
   const unsigned lane = lane_id();
   const uint32_t r = S.round;
   const bool all = (S.ac3_list == NIL);
@@ -662,6 +704,7 @@ __device__ void ac3_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, 
     append_dead(D, B, dies, v, r, Lout);
     append_live(D, B, stays, v, r, Lout);
   }
+  stats_flush(D, K);
 }
 
 // ------------------------------------------------------------------ AC-6
@@ -732,8 +775,9 @@ __device__ unsigned block_sum(unsigned x) {
 // every live vertex re-checks its support position, joins the bulk supporting
 // set of the support it keeps (a counting sort by support: count, grid-wide
 // scan, scatter), or is removed. Three internal grid barriers.
-__device__ bool ac6_entry(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, uint32_t nwarps,
-                          Counters& K) {
+__device__ ROUND_FN bool ac6_entry(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp,
+                                   uint32_t nwarps) {
+  Counters K;
   const unsigned lane = lane_id();
   const uint32_t r = S.round, n = D.n;
   for (uint32_t base = gwarp * 32; base < n; base += nwarps * 32) {
@@ -760,6 +804,7 @@ __device__ bool ac6_entry(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, 
     K.swept += has ? 1 : 0;
     append_dead(D, B, dies, v, r, D.live0);
   }
+  stats_flush(D, K);
   if (!grid_barrier(D, B)) return false;
   // grid-wide exclusive scan of s_cnt into s_off
   const uint32_t chunk = ((n + gridDim.x - 1) / gridDim.x + 31) & ~31u;
@@ -803,9 +848,10 @@ __device__ bool ac6_entry(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, 
   return true;
 }
 
-__device__ bool ac6_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, uint32_t nwarps,
-                          Counters& K) {
-  if (S.prev_variant != TRIM_AC6_SUPPORT) return ac6_entry(D, B, S, gwarp, nwarps, K);
+__device__ ROUND_FN bool ac6_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp,
+                                   uint32_t nwarps) {
+  if (S.prev_variant != TRIM_AC6_SUPPORT) return ac6_entry(D, B, S, gwarp, nwarps);
+  Counters K;
   const unsigned lane = lane_id();
   const uint32_t r = S.round;
   const uint32_t N = S.fe - S.fb;
@@ -865,12 +911,13 @@ __device__ bool ac6_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp, 
       }
     }
   }
+  stats_flush(D, K);
   return true;
 }
 
 // ------------------------------------------------------------------ init (round 0)
 
-__device__ void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32_t nwarps) {
+__device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32_t nwarps) {
   const unsigned lane = lane_id();
   const uint32_t n = D.n;
   const bool w4 = (D.flags & F_AC4_POSSIBLE) != 0;
@@ -891,7 +938,10 @@ __device__ void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32_t nwarps
 
 }  // namespace
 
-__global__ void __launch_bounds__(512, 2) TRIM_KERNEL(Dev D) {
+#ifndef TRIM_MIN_BLOCKS
+#define TRIM_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
   __shared__ Cta B;
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t nwarps = gridDim.x * wpb;
@@ -902,9 +952,10 @@ __global__ void __launch_bounds__(512, 2) TRIM_KERNEL(Dev D) {
     S.variant = NIL; S.prev_variant = NIL;
     S.c4w = 0; S.e_c4 = 0; S.w_end = 0; S.e_end = 0;
     S.ac3_list = NIL; S.live_in_len = 0; S.live_out = 0;
-    S.done = 0; S.fprev = 0;
+    S.done = 0; S.fprev = 0; S.mixed = 0;
     S.m_live = D.m;
     for (int i = 0; i < NFEAT; ++i) S.feat[i] = 0.0f;
+
     for (int w = 0; w < MAX_WARPS; ++w) {
       WarpSlice& x = B.ws[w];
       x.nlog = x.nw4 = x.nedge = x.nlive = x.ncount = 0;
@@ -914,8 +965,18 @@ __global__ void __launch_bounds__(512, 2) TRIM_KERNEL(Dev D) {
     B.epoch = 0;
     B.err = 0;
   }
+#if TRIM_MODES & 8
+  // blob layout W1[32][12] b1 W2[32][32] b2 W3[3][32] b3 mean istd lo hi; W1 and
+  // W2 are stored transposed in shared memory
+  if (D.model != nullptr)
+    for (int i = threadIdx.x; i < TRIM_MLP_NBLOB; i += blockDim.x) {
+      int dst = i;
+      if (i < 384) dst = (i % 12) * 32 + i / 12;
+      else if (i >= 416 && i < 1440) dst = 416 + ((i - 416) % 32) * 32 + (i - 416) / 32;
+      B.model[dst] = __ldg(&D.model[i]);
+    }
+#endif
   __syncthreads();
-  Counters K;
   start_round(D, 0);
   init_round(D, B, gwarp, nwarps);
   flush_round(D, B, 0, D.live0);
@@ -927,24 +988,17 @@ __global__ void __launch_bounds__(512, 2) TRIM_KERNEL(Dev D) {
     if (S.done) break;
     start_round(D, S.round);
     if ((MODES & M_AC4) && S.variant == TRIM_AC4_PUSH) {
-      ac4_round(D, B, S, gwarp, nwarps, K);
+      ac4_round(D, B, S, gwarp, nwarps);
     } else if ((MODES & M_AC6) && S.variant == TRIM_AC6_SUPPORT) {
-      if (!ac6_round(D, B, S, gwarp, nwarps, K)) break;
+      if (!ac6_round(D, B, S, gwarp, nwarps)) break;
     } else if (MODES & M_AC3) {
-      ac3_round(D, B, S, gwarp, nwarps, K);
+      ac3_round(D, B, S, gwarp, nwarps);
     }
+    const bool stamp = (D.flags & F_ROUND_LOG) && blockIdx.x == 0 && threadIdx.x == 0;
+    if (stamp) D.C->t_work[S.round & 3] = globaltimer();
     flush_round(D, B, S.round, S.live_out ? D.live1 : D.live0);
+    if (stamp) D.C->t_flush[S.round & 3] = globaltimer();
     ok = grid_barrier(D, B);
-  }
-  if (D.flags & F_STATS) {
-    const unsigned long long e = warp_sum(K.edges), p = warp_sum(K.pushed),
-                             c = warp_sum(K.cand), s = warp_sum(K.swept);
-    if (lane_id() == 0) {
-      if (e) atomicAdd(&D.C->stats[0], e);
-      if (p) atomicAdd(&D.C->stats[1], p);
-      if (c) atomicAdd(&D.C->stats[2], c);
-      if (s) atomicAdd(&D.C->stats[3], s);
-    }
   }
 }
 

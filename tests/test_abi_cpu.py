@@ -44,7 +44,7 @@ def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(TrimCsr) == 40
     assert ctypes.sizeof(TrimParams) == 32
     assert ctypes.sizeof(TrimRunStats) == 64
-    assert ctypes.sizeof(TrimRoundRec) == 80
+    assert ctypes.sizeof(TrimRoundRec) == 96
 
 
 def test_host_argument_checks_without_device(lib):

@@ -1,0 +1,118 @@
+"""The scheduler MLP's CUDA kernels (forward, loss + gradient, Adam) through the
+C ABI against the double-precision CPU reference, and the in-kernel inference
+that picks each round's variant against the same reference.
+
+Tolerances: the kernels compute in fp32 with FMA; for this 3-layer network with
+O(1) inputs the relative error of logits, loss and gradients stays far below
+1e-3, the bound asserted here."""
+import numpy as np
+import pytest
+
+import graphgen.configs as cfg
+from oracle import mlp_ref as R
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(seed, N, scale=0.4):
+    import torch
+    rng = np.random.default_rng(seed)
+    theta = rng.normal(0, scale, R.NPARAMS).astype(np.float32)
+    X = rng.normal(0, 1, (N, R.NIN)).astype(np.float32)
+    y = rng.integers(0, 3, N).astype(np.uint8)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    return theta, X, y, dev(theta), dev(X), dev(y)
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+@pytest.mark.parametrize("N", [1, 31, 1000, 40000])
+def test_forward_matches_reference(N):
+    import torch
+    import paper_2107_12720_gb300 as P
+    theta, X, y, dt, dX, dy = _setup(10 + N, N)
+    logits = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    P.abi.trim_mlp_forward(dt, dX, N, logits, _stream())
+    want, _ = R.forward(theta.astype(np.float64), X.astype(np.float64))
+    got = logits.cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-4 * max(1.0, np.abs(want).max())
+
+
+@pytest.mark.parametrize("N", [1, 7, 512, 30000])
+def test_loss_and_gradient_match_reference(N):
+    import torch
+    import paper_2107_12720_gb300 as P
+    theta, X, y, dt, dX, dy = _setup(20 + N, N)
+    grad = torch.empty(R.NPARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    scratch = torch.empty(P.abi.trim_mlp_scratch_bytes(N) // 4 + 1, dtype=torch.float32,
+                          device="cuda")
+    P.abi.trim_mlp_loss_grad(dt, dX, dy, N, loss, grad, scratch, _stream())
+    L, g = R.loss_grad(theta.astype(np.float64), X.astype(np.float64), y)
+    gg = grad.cpu().numpy()
+    assert abs(float(loss.item()) - L) <= 1e-4 * max(1.0, abs(L))
+    assert np.abs(gg - g).max() <= 1e-3 * np.abs(g).max()
+    # deterministic: a second call gives the same bits
+    grad2 = torch.empty_like(grad)
+    P.abi.trim_mlp_loss_grad(dt, dX, dy, N, loss, grad2, scratch, _stream())
+    assert torch.equal(grad, grad2)
+
+
+def test_adam_step_matches_reference():
+    import torch
+    import paper_2107_12720_gb300 as P
+    theta, X, y, dt, dX, dy = _setup(7, 256)
+    rng = np.random.default_rng(8)
+    g = rng.normal(0, 0.1, R.NPARAMS).astype(np.float32)
+    m = rng.normal(0, 0.01, R.NPARAMS).astype(np.float32)
+    v = np.abs(rng.normal(0, 0.01, R.NPARAMS)).astype(np.float32)
+    dg, dm, dv = (torch.from_numpy(a.copy()).cuda() for a in (g, m, v))
+    P.abi.trim_mlp_adam_step(dt, dg, dm, dv, 5, 1e-3, 0.9, 0.999, 1e-8, _stream())
+    # the ABI takes the hyper-parameters as fp32: the reference uses the same values
+    f32 = lambda x: float(np.float32(x))
+    th, mm, vv = R.adam_step(theta.astype(np.float64), g.astype(np.float64),
+                             m.astype(np.float64), v.astype(np.float64), 5, f32(1e-3),
+                             f32(0.9), f32(0.999), f32(1e-8))
+    # fp32 rounding bound of each update (a few ulps of the summed magnitudes);
+    # the moments can cancel to near zero, so a relative tolerance alone is wrong
+    eps = np.finfo(np.float32).eps
+    bm = 4 * eps * (0.9 * np.abs(m) + 0.1 * np.abs(g))
+    bv = 4 * eps * (0.999 * np.abs(v) + 0.001 * g * g)
+    assert (np.abs(dm.cpu().numpy() - mm) <= bm + 1e-30).all()
+    assert (np.abs(dv.cpu().numpy() - vv) <= bv + 1e-30).all()
+    step = np.abs(theta.astype(np.float64) - th)
+    assert (np.abs(dt.cpu().numpy() - th) <= 4 * eps * np.abs(th) + 1e-3 * step + 1e-12).all()
+
+
+def test_in_kernel_choice_matches_reference_argmax():
+    """A random model drives TRIM_SCHED_LEARNED; each round's recorded features,
+    normalised and run through the CPU reference, must give the variant the
+    kernel actually ran (rounds whose top two logits are within 1e-3 skipped)."""
+    import paper_2107_12720_gb300 as P
+    rng = np.random.default_rng(99)
+    theta = rng.normal(0, 0.5, R.NPARAMS)
+    mean = rng.normal(0, 1, 12)
+    istd = np.abs(rng.normal(1, 0.2, 12))
+    blob = np.concatenate([theta, mean, istd, np.full(12, -1e30), np.full(12, 1e30)])
+    checked = 0
+    for i in [1, 2]:
+        g = cfg.config_small(i)
+        with P.Trimmer(g.off, g.tgt, flags=P.TRIM_FLAG_ROUND_LOG) as t:
+            t.run("ac4")  # builds G^T so that all three variants are available
+            t.set_model(blob.astype(np.float32))
+            t.run("learned")
+            for rec in t.round_log():
+                f = np.array(rec.features, np.float32)
+                x = (f - mean.astype(np.float32)) * istd.astype(np.float32)
+                z, _ = R.forward(theta.astype(np.float32).astype(np.float64),
+                                 x.astype(np.float64)[None, :])
+                z = z[0]
+                order = np.argsort(z)[::-1]
+                if z[order[0]] - z[order[1]] < 1e-3:
+                    continue
+                assert rec.variant == order[0], (i, rec.round, z, rec.variant)
+                checked += 1
+    assert checked > 10

@@ -62,7 +62,7 @@ def hand_cases():
         "single": gg.edges_from_lists(1, [[]]),
         "single_loop": gg.edges_from_lists(1, [[0]]),
     }
-    # a hub whose in-degree exceeds the AC-4 piece threshold (split into pieces)
+    # a hub with 5,000 in-edges: its AC-4 pushes spread over many warps
     nh = 5000
     cases["big_in_hub"] = gg.edges_from_lists(nh + 1, [[]] + [[0]] * nh)
     # long dead runs before a live successor (warp-cooperative rescans)
@@ -208,3 +208,54 @@ def test_full_configs_all_variants(i):
     with P.Trimmer(off, tgt, oi, ti) as t:
         for v in variants:
             check(t, lvl, st, alpha, v, t.run(v))
+
+
+def test_batch_run_matches_oracle_and_per_graph_runs():
+    """Batched trimming of packed independent graphs (one persistent launch,
+    replayed from a captured CUDA graph) equals the oracle on the union and each
+    graph trimmed alone; repeated calls give identical results."""
+    P = _P()
+    u = cfg.config_small(3)
+    lvl, st, alpha = oracle.peel(u.off, u.tgt)
+    off, tgt = dev_csr(u)
+    with P.Trimmer(off, tgt, flags=P.TRIM_FLAG_VALIDATE) as t:
+        for v in ["ac4", "heuristic", "ac4", "ac6", "ac3"]:
+            for _ in range(3):
+                s = t.batch_run(u.graph_off, v)
+                check(t, lvl, st, alpha, f"batch-{v}", s)
+    go = u.graph_off.astype(np.int64)
+    for gi in range(0, len(go) - 1, 9):
+        a, b = int(go[gi]), int(go[gi + 1])
+        g = gg.Graph(u.off[a:b + 1] - u.off[a], u.tgt[u.off[a]:u.off[b]] - a)
+        with P.Trimmer(g.off, g.tgt) as t:
+            t.run("ac4")
+            assert np.array_equal(t.level(device=False), lvl[a:b])
+
+
+def test_batch_run_rejects_cross_graph_edges():
+    P = _P()
+    u = cfg.config_small(3)
+    tgt = u.tgt.copy()
+    go = u.graph_off
+    e0 = int(u.off[int(go[1])])        # first out-edge of graph 1 ...
+    tgt[e0] = int(go[0])               # ... now points into graph 0
+    with P.Trimmer(u.off, tgt, flags=P.TRIM_FLAG_VALIDATE) as t:
+        with pytest.raises(P.TrimError) as e:
+            t.batch_run(go, "ac4")
+        assert e.value.code == 2
+    with P.Trimmer(u.off, u.tgt) as t:
+        with pytest.raises(P.TrimError) as e:
+            t.batch_run(np.array([0, 5], np.uint32), "ac4")  # does not end at n
+        assert e.value.code == 1
+
+
+def test_full_batched_workload():
+    """The batched workload at full size (4,096 packed planted graphs, 22M
+    vertices), trimmed in one batched launch, against the oracle."""
+    P = _P()
+    u = cfg.config(3)
+    lvl, st, alpha = oracle.peel(u.off, u.tgt)
+    off, tgt = dev_csr(u)
+    with P.Trimmer(off, tgt) as t:
+        for v in ["ac4", "heuristic"]:
+            check(t, lvl, st, alpha, f"batch-{v}", t.batch_run(u.graph_off, v))
