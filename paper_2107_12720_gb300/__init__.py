@@ -33,6 +33,15 @@ VARIANTS = {"ac4": TRIM_AC4_PUSH, "ac6": TRIM_AC6_SUPPORT, "ac3": TRIM_AC3_PULL,
 __all__ = ["Trimmer", "TrimError", "VARIANTS", "lib", "LIB_PATH"]
 
 
+def _as_u32(a) -> np.ndarray:
+    """A uint32 view of a 32-bit integer array (no copy: a pinned host buffer
+    stays pinned); other dtypes or layouts are converted."""
+    a = np.asarray(a)
+    if a.dtype in (np.int32, np.uint32) and a.flags.c_contiguous:
+        return a.view(np.uint32)
+    return np.ascontiguousarray(a, np.uint32)
+
+
 def _variant(v) -> int:
     if isinstance(v, str):
         return VARIANTS[v]
@@ -75,8 +84,7 @@ class Trimmer:
         if isinstance(off, torch.Tensor):
             off = off.numpy()
             tgt = tgt.numpy()
-        off = np.ascontiguousarray(off, np.uint32)
-        tgt = np.ascontiguousarray(tgt, np.uint32)
+        off, tgt = _as_u32(off), _as_u32(tgt)
         self._keep += [off, tgt]
         return TrimCsr(off.shape[0] - 1, tgt.shape[0], off.ctypes.data,
                        tgt.ctypes.data if tgt.size else None, 0)

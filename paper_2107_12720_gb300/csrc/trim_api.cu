@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -56,6 +57,7 @@ struct trim_ctx {
   cudaStream_t cap_stream = nullptr;      // private stream used only for that capture
   bool capturing = false;
   int batch_variant = -1;
+  int batch_last_variant = -1;
   uint64_t batch_graph_launches = 0;
   bool ran = false;
   bool pending = false;
@@ -85,22 +87,66 @@ trim_err_t cuda_fail(trim_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);        \
   } while (0)
 
+// Device memory comes from a stream-ordered pool owned by the library (one per
+// device): freeing a context returns its memory to the pool instead of
+// unmapping it, so creating and destroying contexts stays cheap. Up to
+// kPoolKeepBytes stay reserved between contexts; the rest goes back to the
+// system at the next synchronisation.
+constexpr uint64_t kPoolKeepBytes = 4ull << 30;
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaError_t device_pool(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = kPoolKeepBytes;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) return e;
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+
 template <class T>
 trim_err_t dalloc(trim_ctx* c, T** p, size_t count) {
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
   if (g_alloc_limit && c->allocated + bytes > g_alloc_limit)
     return fail(c, TRIM_ERR_OOM, "device memory cap reached");
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = device_pool(c->device, &pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&q, bytes, pool, c->stream);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
-    return cuda_fail(c, e, "cudaMalloc");
+    return cuda_fail(c, e, "cudaMallocFromPoolAsync");
   }
   c->owned.push_back(q);
   c->allocated += bytes;
   *p = static_cast<T*>(q);
   return TRIM_OK;
 }
+
+// Carves 256-byte aligned pieces out of one device allocation (an "arena"),
+// so a context costs one cudaMalloc and one cudaFree instead of one per array.
+struct ArenaPlan {
+  size_t bytes = 0;
+  template <class T>
+  size_t add(size_t count) {
+    const size_t at = bytes;
+    bytes += (std::max<size_t>(count, 1) * sizeof(T) + 255) & ~size_t(255);
+    return at;
+  }
+};
 
 #define TRY(x)                       \
   do {                               \
@@ -113,9 +159,9 @@ void release(trim_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  for (void* p : c->owned) cudaFree(p);
+  for (void* p : c->owned) cudaFreeAsync(p, c->stream);
   c->owned.clear();
-  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  delete c->h_ctrl;
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
 }
@@ -160,7 +206,24 @@ typedef void (*persistent_fn)(trimk::Dev);
 const persistent_fn kFlavours[4] = {trim_persistent_kernel_m1, trim_persistent_kernel_m2,
                                     trim_persistent_kernel_m4, trim_persistent_kernel_m15};
 
+// launch shapes are a property of the device and the block size: computed once
+// per (device, block_threads, ctas_per_sm) for the whole process
+struct GridCache {
+  int device = -1;
+  uint32_t block = 0, cps = 0;
+  int grids[4] = {0, 0, 0, 0};
+};
+std::mutex g_grid_mutex;
+GridCache g_grid_cache[8];
+
 trim_err_t compute_grid(trim_ctx* c) {
+  std::lock_guard<std::mutex> lock(g_grid_mutex);
+  for (const GridCache& e : g_grid_cache)
+    if (e.device == c->device && e.block == c->params.block_threads &&
+        e.cps == c->params.ctas_per_sm) {
+      for (int k = 0; k < 4; ++k) c->grids[k] = e.grids[k];
+      return TRIM_OK;
+    }
   for (int k = 0; k < 4; ++k) {
     int per_sm = 0;
     CK(cudaFuncSetAttribute(kFlavours[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -172,6 +235,14 @@ trim_err_t compute_grid(trim_ctx* c) {
     if (c->params.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)c->params.ctas_per_sm);
     c->grids[k] = per_sm * c->sm_count;
   }
+  for (GridCache& e : g_grid_cache)
+    if (e.device < 0) {
+      e.device = c->device;
+      e.block = c->params.block_threads;
+      e.cps = c->params.ctas_per_sm;
+      for (int k = 0; k < 4; ++k) e.grids[k] = c->grids[k];
+      break;
+    }
   return TRIM_OK;
 }
 
@@ -273,23 +344,6 @@ trim_err_t validate(trim_ctx* c, const uint32_t* ioff_given) {
   return TRIM_OK;
 }
 
-trim_err_t upload(trim_ctx* c, const trim_csr_t* g, const uint32_t** off, const uint32_t** tgt) {
-  if (g->on_device) {
-    *off = g->offsets;
-    *tgt = g->targets;
-    return TRIM_OK;
-  }
-  uint32_t *o = nullptr, *t = nullptr;
-  TRY(dalloc(c, &o, (size_t)g->n + 1));
-  TRY(dalloc(c, &t, g->m));
-  CK(cudaMemcpyAsync(o, g->offsets, ((size_t)g->n + 1) * 4, cudaMemcpyHostToDevice, c->stream));
-  if (g->m) CK(cudaMemcpyAsync(t, g->targets, g->m * 4, cudaMemcpyHostToDevice, c->stream));
-  TRY(sync_check(c));
-  *off = o;
-  *tgt = t;
-  return TRIM_OK;
-}
-
 trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, uint32_t flags,
                        trim_ctx* c) {
   if (g->n > 0xFFFFFFFEu || g->m >= (1ull << 32))
@@ -315,30 +369,61 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
   default_params(&c->params);
   CK(cudaEventCreate(&c->ev0));
   CK(cudaEventCreate(&c->ev1));
-  TRY(upload(c, g, &c->off, &c->tgt));
-  if (gi) TRY(upload(c, gi, &c->ioff, &c->itgt));
-  if (flags & TRIM_FLAG_VALIDATE) TRY(validate(c, gi ? c->ioff : nullptr));
+  // one arena: copies of host inputs, then all per-run state
   const size_t n = c->n;
-  TRY(dalloc(c, &c->level, n));
-  TRY(dalloc(c, &c->cnt, n));
-  TRY(dalloc(c, &c->supp, n));
-  TRY(dalloc(c, &c->s_head, n));
-  TRY(dalloc(c, &c->s_next, n));
-  TRY(dalloc(c, &c->s_cnt, n));
-  TRY(dalloc(c, &c->s_off, n + 1));
-  TRY(dalloc(c, &c->s_list, n));
-  TRY(dalloc(c, &c->log, n));
-  TRY(dalloc(c, &c->roff, n + 2));
-  TRY(dalloc(c, &c->live0, n));
-  TRY(dalloc(c, &c->live1, n));
-  TRY(dalloc(c, &c->bsum, 8192));
-  TRY(dalloc(c, &c->ctrl, 1));
-  CK(cudaMemsetAsync(c->s_cnt, 0, n * 4, c->stream));
-  CK(cudaMallocHost(&c->h_ctrl, sizeof(Ctrl)));
-  if (flags & TRIM_FLAG_ROUND_LOG) {
-    c->rlog_cap = (uint32_t)std::min<uint64_t>(n + 1, 1u << 20);
-    TRY(dalloc(c, &c->rlog, c->rlog_cap));
+  if (flags & TRIM_FLAG_ROUND_LOG) c->rlog_cap = (uint32_t)std::min<uint64_t>(n + 1, 1u << 20);
+  ArenaPlan A;
+  const size_t a_off = g->on_device ? 0 : A.add<uint32_t>(n + 1);
+  const size_t a_tgt = g->on_device ? 0 : A.add<uint32_t>(c->m);
+  const bool in_host = gi && !gi->on_device;
+  const size_t a_ioff = in_host ? A.add<uint32_t>(n + 1) : 0;
+  const size_t a_itgt = in_host ? A.add<uint32_t>(c->m) : 0;
+  const size_t a_level = A.add<uint32_t>(n), a_cnt = A.add<uint32_t>(n), a_supp = A.add<uint32_t>(n);
+  const size_t a_shead = A.add<uint32_t>(n), a_snext = A.add<uint32_t>(n);
+  const size_t a_scnt = A.add<uint32_t>(n), a_soff = A.add<uint32_t>(n + 1);
+  const size_t a_slist = A.add<uint32_t>(n), a_log = A.add<uint32_t>(n);
+  const size_t a_roff = A.add<uint32_t>(n + 2), a_live0 = A.add<uint32_t>(n);
+  const size_t a_live1 = A.add<uint32_t>(n), a_bsum = A.add<uint32_t>(8192);
+  const size_t a_ctrl = A.add<Ctrl>(1);
+  const size_t a_w4r = A.add<uint32_t>(n), a_w4e = A.add<uint32_t>(n);
+  const size_t a_chunk = A.add<uint32_t>((c->m >> 5) + 2);
+  const size_t a_rlog = c->rlog_cap ? A.add<trim_round_rec_t>(c->rlog_cap) : 0;
+  char* base = nullptr;
+  TRY(dalloc(c, &base, A.bytes));
+  auto at = [&](size_t o) { return reinterpret_cast<uint32_t*>(base + o); };
+  if (!g->on_device) {
+    CK(cudaMemcpyAsync(at(a_off), g->offsets, (n + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+    if (c->m)
+      CK(cudaMemcpyAsync(at(a_tgt), g->targets, c->m * 4, cudaMemcpyHostToDevice, c->stream));
+    c->off = at(a_off);
+    c->tgt = at(a_tgt);
+  } else {
+    c->off = g->offsets;
+    c->tgt = g->targets;
   }
+  if (gi) {
+    if (in_host) {
+      CK(cudaMemcpyAsync(at(a_ioff), gi->offsets, (n + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+      if (c->m)
+        CK(cudaMemcpyAsync(at(a_itgt), gi->targets, c->m * 4, cudaMemcpyHostToDevice, c->stream));
+      c->ioff = at(a_ioff);
+      c->itgt = at(a_itgt);
+    } else {
+      c->ioff = gi->offsets;
+      c->itgt = gi->targets;
+    }
+  }
+  c->level = at(a_level); c->cnt = at(a_cnt); c->supp = at(a_supp);
+  c->s_head = at(a_shead); c->s_next = at(a_snext); c->s_cnt = at(a_scnt);
+  c->s_off = at(a_soff); c->s_list = at(a_slist); c->log = at(a_log); c->roff = at(a_roff);
+  c->live0 = at(a_live0); c->live1 = at(a_live1); c->bsum = at(a_bsum);
+  c->ctrl = reinterpret_cast<Ctrl*>(base + a_ctrl);
+  c->w4_row = at(a_w4r); c->w4_eoff = at(a_w4e); c->chunk_first = at(a_chunk);
+  if (c->rlog_cap) c->rlog = reinterpret_cast<trim_round_rec_t*>(base + a_rlog);
+  if (flags & TRIM_FLAG_VALIDATE) TRY(validate(c, gi ? c->ioff : nullptr));
+  CK(cudaMemsetAsync(c->s_cnt, 0, n * 4, c->stream));
+  c->h_ctrl = new (std::nothrow) Ctrl();
+  if (!c->h_ctrl) return fail(c, TRIM_ERR_OOM, "host allocation failed");
   TRY(compute_grid(c));
   TRY(sync_check(c));
   return TRIM_OK;
@@ -347,7 +432,7 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
 // AC-4 work list (one entry per removed vertex with in-edges) and the owner
 // index of every 32-edge chunk of its in-edge prefix; allocated on first use.
 trim_err_t ensure_work_list(trim_ctx* c) {
-  if (c->w4_row) return TRIM_OK;
+  if (c->w4_row) return TRIM_OK;  // carved from the arena at create time
   TRY(dalloc(c, &c->w4_row, c->n));
   TRY(dalloc(c, &c->w4_eoff, c->n));
   TRY(dalloc(c, &c->chunk_first, (c->m >> 5) + 2));
@@ -504,8 +589,14 @@ trim_err_t enqueue_batch(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
   (void)graph_off;
   (void)G;
   if (c->batch_exec == nullptr || c->batch_variant != (int)variant) {
-    // one direct run first: builds G^T if needed, sizes the work list, and
-    // leaves all allocations in place before the capture
+    // the first call with a variant runs directly (a one-shot caller pays no
+    // capture); the second captures, then every later call replays the graph.
+    // The direct run also builds G^T if needed and leaves all allocations in
+    // place before the capture.
+    if (c->batch_last_variant != (int)variant) {
+      c->batch_last_variant = (int)variant;
+      return enqueue_run(c, variant);
+    }
     TRY(enqueue_run(c, variant));
     TRY(finish_run(c, nullptr));
     if (c->batch_exec) {
