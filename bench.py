@@ -357,8 +357,11 @@ def run_ours(args, rank, ws, local):
 
     sweep = {}
     if args.sweep and rank == 0:
-        for v in ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if have_model else []):
-            ts, ks, st = time_variant(P, t, v, max(20, args.steps // 10), 3, flush, gofs)
+        names = args.sweep_variants.split(",") if args.sweep_variants else \
+            ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if have_model else [])
+        for v in names:
+            ts, ks, st = time_variant(P, t, v, max(args.sweep_steps, args.steps // 10), 1, flush,
+                                      gofs)
             sweep[v] = {"ms": statistics.mean(ts), "kernel_ms": statistics.mean(ks),
                         "edges_per_s": g.m / (statistics.mean(ts) * 1e-3),
                         "rounds_by_variant": st["rounds_by_variant"]}
@@ -438,6 +441,8 @@ def main(argv=None):
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--variant", default=None)
     ap.add_argument("--sweep", action="store_true", help="also time every variant (stderr + JSON)")
+    ap.add_argument("--sweep-variants", default="", help="comma-separated subset for --sweep")
+    ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

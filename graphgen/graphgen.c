@@ -52,22 +52,36 @@ uint64_t gg_word(uint64_t seed, uint64_t stream, uint64_t i) {
 
 /* ---------- bijections (pseudo-random permutations) ---------- */
 
-/* A bijection on [0, 2^k): rounds of (multiply by odd) (xor-shift) (add). */
-static inline uint64_t perm_pow2(uint64_t x, int k, uint64_t pkey) {
-  const uint64_t mask = (k >= 64) ? ~0ull : ((1ull << k) - 1);
-  const int s = (k + 1) / 2 > 0 ? (k + 1) / 2 : 1;
+/* A bijection on [0, 2^k): rounds of (multiply by odd) (xor-shift) (add);
+ * the round constants are words 0..7 of the key's stream. */
+typedef struct { uint64_t a[4], c[4], mask; int s; } perm_consts;
+static inline void perm_setup(perm_consts* P, int k, uint64_t pkey) {
+  P->mask = (k >= 64) ? ~0ull : ((1ull << k) - 1);
+  P->s = (k + 1) / 2 > 0 ? (k + 1) / 2 : 1;
   for (int r = 0; r < 4; ++r) {
-    uint64_t a = word_at(pkey, 2 * r) | 1ull, c = word_at(pkey, 2 * r + 1);
-    x = (x * a) & mask;
-    x ^= x >> s;
-    x = (x + c) & mask;
+    P->a[r] = word_at(pkey, 2 * r) | 1ull;
+    P->c[r] = word_at(pkey, 2 * r + 1);
+  }
+}
+static inline uint64_t perm_apply(const perm_consts* P, uint64_t x) {
+  for (int r = 0; r < 4; ++r) {
+    x = (x * P->a[r]) & P->mask;
+    x ^= x >> P->s;
+    x = (x + P->c[r]) & P->mask;
   }
   return x;
+}
+static inline uint64_t perm_pow2(uint64_t x, int k, uint64_t pkey) {
+  perm_consts P;
+  perm_setup(&P, k, pkey);
+  return perm_apply(&P, x);
 }
 static int ceil_log2(uint64_t n) { int k = 0; while ((1ull << k) < n) ++k; return k; }
 /* Bijection on [0,n) by cycle-walking the power-of-two bijection. */
 static inline uint64_t perm_n(uint64_t x, uint64_t n, int k, uint64_t pkey) {
-  do { x = perm_pow2(x, k, pkey); } while (x >= n);
+  perm_consts P;
+  perm_setup(&P, k, pkey);
+  do { x = perm_apply(&P, x); } while (x >= n);
   return x;
 }
 
@@ -236,6 +250,7 @@ static inline void rmat_draw(uint64_t key, int scale, uint32_t ta, uint32_t tab,
 
 typedef struct {
   uint64_t seed, pkey, skey;
+  perm_consts pid, psink;
   int scale;
   uint32_t n, nsinks, ta, tab, tabc;
 } rmat_ctx;
@@ -244,6 +259,8 @@ static void rmat_setup(uint64_t seed, const gg_rmat_params* p, rmat_ctx* c) {
   c->seed = seed; c->scale = p->scale; c->n = 1u << p->scale;
   c->pkey = stream_key(seed, 0xA11CEull);
   c->skey = stream_key(seed, 0x5111Cull);
+  perm_setup(&c->pid, p->scale, c->pkey);
+  perm_setup(&c->psink, p->scale, c->skey);
   c->nsinks = (uint32_t)(p->sink_frac * (double)c->n);
   c->ta = (uint32_t)(p->a * 65536.0 + 0.5);
   c->tab = (uint32_t)((p->a + p->b) * 65536.0 + 0.5);
@@ -253,10 +270,10 @@ static void rmat_setup(uint64_t seed, const gg_rmat_params* p, rmat_ctx* c) {
 static inline int rmat_edge(const rmat_ctx* c, uint64_t i, uint32_t* s, uint32_t* d) {
   uint32_t s0, d0;
   rmat_draw(stream_key(c->seed, (1ull << 62) + i), c->scale, c->ta, c->tab, c->tabc, &s0, &d0);
-  uint32_t s1 = (uint32_t)perm_pow2(s0, c->scale, c->pkey);
-  uint32_t d1 = (uint32_t)perm_pow2(d0, c->scale, c->pkey);
+  uint32_t s1 = (uint32_t)perm_apply(&c->pid, s0);
+  uint32_t d1 = (uint32_t)perm_apply(&c->pid, d0);
   if (s1 == d1) return 0;
-  if (perm_pow2(s1, c->scale, c->skey) < c->nsinks) return 0;
+  if (perm_apply(&c->psink, s1) < c->nsinks) return 0;
   *s = s1; *d = d1;
   return 1;
 }

@@ -108,7 +108,8 @@ typedef struct {
   uint64_t candidates;      /* TRIM_FLAG_STATS: AC-6 supporting-set members re-scanned     */
   uint64_t live_swept;      /* TRIM_FLAG_STATS: AC-3 live-list entries visited             */
   uint32_t rounds_by_variant[3]; /* rounds run by AC-4, AC-6, AC-3                         */
-  uint32_t reserved;
+  uint32_t segments;        /* persistent-kernel launches of the run (1 unless a scheduled
+                               trim_run switched between variant kernels)               */
 } trim_run_stats_t;
 
 /* One record per round of a TRIM_FLAG_ROUND_LOG run. features[] are the
@@ -137,11 +138,19 @@ trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void
                        uint32_t flags, trim_ctx** out);
 
 /* Runs the whole trimming (all rounds) with the given variant or scheduler.
- * Returns once status/level are final on the device. stats may be NULL. */
+ * Returns once status/level are final on the device. stats may be NULL.
+ * A fixed variant runs as one persistent launch of a kernel that holds only that
+ * variant. A scheduled run (HEURISTIC, LEARNED, SCRIPTED) runs as segments: each
+ * one launch of the kernel that holds one variant plus the schedulers; when the
+ * scheduler picks another variant the kernel saves the schedule state and exits,
+ * and the next segment resumes at the same round (the host waits between
+ * segments). The result is the same as that of the single all-variant launch
+ * that trim_run_async uses. */
 trim_err_t trim_run(trim_ctx* ctx, trim_variant_t variant, trim_run_stats_t* stats);
 
 /* Enqueues the same work as trim_run without waiting (no host synchronisation,
- * so it may be captured into a CUDA graph). Errors raised on the device surface
+ * so it may be captured into a CUDA graph): one persistent launch, for a
+ * scheduled run that of the kernel holding all three variants. Errors raised on the device surface
  * at the next trim_sync(). */
 trim_err_t trim_run_async(trim_ctx* ctx, trim_variant_t variant);
 /* Waits for the enqueued work and reports its device-side status; stats may be NULL. */
@@ -254,7 +263,7 @@ trim_err_t trim_mlp_adam_step(float* params, const float* grad, float* m, float*
  * cuda_stream before it returns, to report device-side errors. */
 #define TRIM_NOALLOC_MAX_N (1u << 18)
 #define TRIM_NOALLOC_MAX_M (1u << 22)
-#define TRIM_NOALLOC_SCRATCH_BYTES 5768960u
+#define TRIM_NOALLOC_SCRATCH_BYTES 5769216u
 trim_err_t trim_run_ac4_noalloc(const uint32_t* offsets, const uint32_t* targets,
                                 const uint32_t* in_offsets, const uint32_t* in_targets,
                                 uint32_t n, uint32_t m, uint32_t* level_out,

@@ -21,6 +21,9 @@ LIB = os.path.join(HERE, "libtrim.so")
 UNITS = [("trim_kernels.cu", ["-DTRIM_MODES=1"], "trim_kernels_m1.o"),
          ("trim_kernels.cu", ["-DTRIM_MODES=2"], "trim_kernels_m2.o"),
          ("trim_kernels.cu", ["-DTRIM_MODES=4"], "trim_kernels_m4.o"),
+         ("trim_kernels.cu", ["-DTRIM_MODES=9"], "trim_kernels_m9.o"),
+         ("trim_kernels.cu", ["-DTRIM_MODES=10"], "trim_kernels_m10.o"),
+         ("trim_kernels.cu", ["-DTRIM_MODES=12"], "trim_kernels_m12.o"),
          ("trim_kernels.cu", ["-DTRIM_MODES=15"], "trim_kernels_m15.o"),
          ("trim_aux.cu", [], "trim_aux.o"),
          ("trim_api.cu", [], "trim_api.o"),

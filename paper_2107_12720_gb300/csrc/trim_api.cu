@@ -51,8 +51,12 @@ struct trim_ctx {
   uint32_t script_len = 0;
   uint8_t* status_tmp = nullptr;
   trim_params_t params{};
-  int grids[4] = {0, 0, 0, 0};
+  int grids[7] = {0, 0, 0, 0, 0, 0, 0};
   int last_flavour = 3;
+  trimk::Dev last_dev{};        // arguments of the last launch (segments reuse them)
+  int seg_first[3] = {-1, -1, -1};  // per scheduled mode: flavour of its last first round
+  uint64_t last_segments = 0;       // kernel launches of the last trim_run
+  std::vector<uint8_t> h_script;    // host copy of the scripted schedule
   cudaGraphExec_t batch_exec = nullptr;  // captured batched launch (trim_batch_run)
   cudaStream_t cap_stream = nullptr;      // private stream used only for that capture
   bool capturing = false;
@@ -201,17 +205,23 @@ constexpr uint32_t kSliceEntries = 256;
 constexpr uint32_t kSbufCap = kSliceEntries;
 size_t dyn_smem_bytes() { return 16 * 4 * (size_t)kSliceEntries * sizeof(uint32_t); }
 
-// kernel flavours: index 0..3 = AC-4 only, AC-6 only, AC-3 only, everything
+// kernel flavours: index 0..3 = AC-4 only, AC-6 only, AC-3 only, everything;
+// 4..6 = AC-4, AC-6, AC-3 each with the per-round schedulers (segments)
 typedef void (*persistent_fn)(trimk::Dev);
-const persistent_fn kFlavours[4] = {trim_persistent_kernel_m1, trim_persistent_kernel_m2,
-                                    trim_persistent_kernel_m4, trim_persistent_kernel_m15};
+constexpr int kNumFlavours = 7;
+constexpr int kFlavourAll = 3;
+constexpr int kFlavourSeg = 4;  // + variant
+const persistent_fn kFlavours[kNumFlavours] = {
+    trim_persistent_kernel_m1,  trim_persistent_kernel_m2,  trim_persistent_kernel_m4,
+    trim_persistent_kernel_m15, trim_persistent_kernel_m9,  trim_persistent_kernel_m10,
+    trim_persistent_kernel_m12};
 
 // launch shapes are a property of the device and the block size: computed once
 // per (device, block_threads, ctas_per_sm) for the whole process
 struct GridCache {
   int device = -1;
   uint32_t block = 0, cps = 0;
-  int grids[4] = {0, 0, 0, 0};
+  int grids[kNumFlavours] = {};
 };
 std::mutex g_grid_mutex;
 GridCache g_grid_cache[8];
@@ -221,10 +231,10 @@ trim_err_t compute_grid(trim_ctx* c) {
   for (const GridCache& e : g_grid_cache)
     if (e.device == c->device && e.block == c->params.block_threads &&
         e.cps == c->params.ctas_per_sm) {
-      for (int k = 0; k < 4; ++k) c->grids[k] = e.grids[k];
+      for (int k = 0; k < kNumFlavours; ++k) c->grids[k] = e.grids[k];
       return TRIM_OK;
     }
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kNumFlavours; ++k) {
     int per_sm = 0;
     CK(cudaFuncSetAttribute(kFlavours[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)dyn_smem_bytes()));
@@ -240,7 +250,7 @@ trim_err_t compute_grid(trim_ctx* c) {
       e.device = c->device;
       e.block = c->params.block_threads;
       e.cps = c->params.ctas_per_sm;
-      for (int k = 0; k < 4; ++k) e.grids[k] = c->grids[k];
+      for (int k = 0; k < kNumFlavours; ++k) e.grids[k] = c->grids[k];
       break;
     }
   return TRIM_OK;
@@ -439,7 +449,9 @@ trim_err_t ensure_work_list(trim_ctx* c) {
   return TRIM_OK;
 }
 
-trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
+// Enqueues one run. A scheduled variant runs on the all-variant kernel, or with
+// seg_flavour >= 0 as the first segment of a segmented run (run_segmented).
+trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1) {
   if ((int)variant < 0 || variant > TRIM_SCHED_SCRIPTED)
     return fail(c, TRIM_ERR_INVALID_ARG, "unknown variant");
   if (variant == TRIM_SCHED_SCRIPTED && c->script_len == 0)
@@ -460,10 +472,8 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
   if ((c->flags & TRIM_FLAG_ROUND_LOG) && variant >= TRIM_SCHED_HEURISTIC)
     f |= trimk::F_NEED_FEATURES;
   if (variant == TRIM_SCHED_SCRIPTED) {
-    std::vector<uint8_t> s(c->script_len);
-    CK(cudaMemcpy(s.data(), c->script, c->script_len, cudaMemcpyDeviceToHost));
     ac4 = ac6 = ac3 = false;
-    for (uint8_t x : s) {
+    for (uint8_t x : c->h_script) {
       if (x == TRIM_AC4_PUSH) ac4 = true;
       else if (x == TRIM_AC6_SUPPORT) ac6 = true;
       else ac3 = true;
@@ -503,10 +513,12 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
   D.spin_limit_ns = c->params.spin_limit_ns;
   D.heur_push_ratio = c->params.heur_push_ratio;
   D.heur_ac6_ratio = c->params.heur_ac6_ratio;
-  // the lean single-variant flavours unless features or a per-round schedule are needed
-  int flavour = 3;
+  // a fixed variant runs on its lean single-variant flavour
+  int flavour = kFlavourAll;
   if (variant <= TRIM_AC3_PULL) flavour = (int)variant;
+  else if (seg_flavour >= 0) flavour = seg_flavour;
   c->last_flavour = flavour;
+  c->last_dev = D;
   const int grid = c->grids[flavour];
   if ((uint32_t)grid > 8192) return fail(c, TRIM_ERR_INVALID_ARG, "grid too large");
   trim_reset_ctrl_kernel<<<1, 32, 0, c->stream>>>(c->ctrl);
@@ -526,10 +538,64 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant) {
   return TRIM_OK;
 }
 
-trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats) {
-  if (c->pending) {
+// Launches the next segment of a segmented run: the flavour of the variant the
+// scheduler picked, resuming from the schedule state the last segment saved.
+trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base) {
+  trimk::Dev D = c->last_dev;
+  D.resume = 1;
+  D.bar_base = bar_base;
+  c->last_flavour = flavour;
+  void* args[] = {&D};
+  CK(cudaLaunchCooperativeKernel((const void*)kFlavours[flavour], dim3(c->grids[flavour]),
+                                 dim3(c->params.block_threads), args, dyn_smem_bytes(),
+                                 c->stream));
+  CK(cudaEventRecord(c->ev1, c->stream));
+  return TRIM_OK;
+}
+
+trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read = false);
+
+// A scheduled run (heuristic, learned, scripted) on the lean kernels: each
+// segment is one cooperative launch of the flavour that holds one variant plus
+// the schedulers. When the scheduler picks a variant the running kernel lacks,
+// the kernel saves the schedule state and exits; the host reads the handover
+// and launches the flavour of that variant, which resumes at the same round.
+// The first segment starts on the flavour this mode's last run started with.
+trim_err_t run_segmented(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats) {
+  const int mi = (int)variant - (int)TRIM_SCHED_HEURISTIC;
+  int first = c->seg_first[mi];
+  if (first < 0 && variant == TRIM_SCHED_SCRIPTED && !c->h_script.empty())
+    first = kFlavourSeg + std::min<int>(c->h_script[0], TRIM_AC3_PULL);
+  if (first < 0) first = kFlavourSeg + (c->ioff ? TRIM_AC4_PUSH : TRIM_AC3_PULL);
+  TRY(enqueue_run(c, variant, first));
+  if (!c->pending) return finish_run(c, stats);
+  uint64_t segments = 1;
+  while (true) {
     TRY(sync_check(c));
     CK(cudaMemcpy(c->h_ctrl, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    const Ctrl& h = *c->h_ctrl;
+    if (h.err || !h.resume) break;
+    if (h.resume_variant > TRIM_AC3_PULL || ++segments > (uint64_t)c->n + 3) {
+      c->pending = false;
+      c->s_cnt_dirty = true;
+      return fail(c, TRIM_ERR_STATE, "invalid segment handover");
+    }
+    const int next = kFlavourSeg + (int)h.resume_variant;
+    if (h.saved.round == 1) c->seg_first[mi] = next;
+    TRY(launch_segment(c, next, h.bar));
+  }
+  c->last_segments = segments;
+  return finish_run(c, stats, true);
+}
+
+// Waits for the enqueued run and publishes its statistics (ctrl_read: the
+// control block is already in h_ctrl).
+trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read) {
+  if (c->pending) {
+    if (!ctrl_read) {
+      TRY(sync_check(c));
+      CK(cudaMemcpy(c->h_ctrl, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    }
     c->pending = false;
     const Ctrl& h = *c->h_ctrl;
     if (h.err) {
@@ -551,6 +617,7 @@ trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats) {
     s.candidates = h.stats[2];
     s.live_swept = h.stats[3];
     for (int i = 0; i < 3; ++i) s.rounds_by_variant[i] = h.vcount[i];
+    s.segments = (uint32_t)c->last_segments;
     c->last = s;
     c->ran = true;
   }
@@ -664,12 +731,16 @@ trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void
 
 trim_err_t trim_run(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats) {
   if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  c->last_segments = 1;
+  if (variant >= TRIM_SCHED_HEURISTIC && variant <= TRIM_SCHED_SCRIPTED)
+    return run_segmented(c, variant, stats);
   TRY(enqueue_run(c, variant));
   return finish_run(c, stats);
 }
 
 trim_err_t trim_run_async(trim_ctx* c, trim_variant_t variant) {
   if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  c->last_segments = 1;
   return enqueue_run(c, variant);
 }
 
@@ -687,6 +758,7 @@ trim_err_t trim_batch_run(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
     if (graph_off[g + 1] < graph_off[g])
       return fail(c, TRIM_ERR_INVALID_ARG, "graph_off must be non-decreasing");
   if (c->flags & TRIM_FLAG_VALIDATE) TRY(validate_batch(c, graph_off, G));
+  c->last_segments = 1;
   TRY(enqueue_batch(c, graph_off, G, variant));
   return finish_run(c, stats);
 }
@@ -798,6 +870,8 @@ trim_err_t trim_set_schedule(trim_ctx* c, const uint8_t* v, uint32_t len) {
   if (len) CK(cudaMemcpyAsync(c->script, v, len, cudaMemcpyHostToDevice, c->stream));
   TRY(sync_check(c));
   c->script_len = len;
+  c->h_script.assign(v, v + len);
+  c->seg_first[TRIM_SCHED_SCRIPTED - TRIM_SCHED_HEURISTIC] = -1;
   return TRIM_OK;
 }
 

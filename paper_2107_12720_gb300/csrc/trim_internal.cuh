@@ -38,24 +38,6 @@ struct RoundStat {
   unsigned int pad[2];
 };
 
-// Global control block. Counters hit by every CTA sit on their own 128-byte lines.
-struct Ctrl {
-  unsigned int bar;       unsigned int _p0[31];  // monotone grid-barrier arrivals
-  unsigned int log_len;   unsigned int _p1[31];  // entries in the dead log
-  unsigned long long w4;  unsigned int _p1b[30];  // AC-4 work list: items (low 32) | edges (high 32)
-  unsigned int err;       unsigned int err_info; unsigned int _p2[30];
-  // published by CTA 0 for the host
-  unsigned int rounds;    // alpha
-  unsigned int vcount[3];
-  unsigned int rlog_len;
-  unsigned int _p3[27];
-  unsigned long long t_round[4];  // CTA 0's %globaltimer at the start of round r (ring)
-  unsigned long long t_work[4];   // ... when CTA 0 finished the work of round r
-  unsigned long long t_flush[4];  // ... when CTA 0 finished flushing round r
-  unsigned long long stats[4];    // edges inspected, in-edges pushed, candidates, live swept
-  RoundStat rs[4];
-};
-
 // The schedule state of the current round. Every CTA keeps its own copy in
 // shared memory and advances it from the same global inputs after each grid
 // barrier, so all copies stay identical without a serial hand-off.
@@ -76,6 +58,31 @@ struct Sched {
   uint32_t mixed;         // 1 once a round ran AC-6 or AC-3 (AC-4 must then re-check levels)
   unsigned long long m_live;     // out-edges of live vertices
   float feat[12];                // features that chose this round's variant
+};
+
+// Global control block. Counters hit by every CTA sit on their own 128-byte lines.
+struct Ctrl {
+  unsigned int bar;       unsigned int _p0[31];  // monotone grid-barrier arrivals
+  unsigned int log_len;   unsigned int _p1[31];  // entries in the dead log
+  unsigned long long w4;  unsigned int _p1b[30];  // AC-4 work list: items (low 32) | edges (high 32)
+  unsigned int err;       unsigned int err_info; unsigned int _p2[30];
+  // published by CTA 0 for the host
+  unsigned int rounds;    // alpha
+  unsigned int vcount[3];
+  unsigned int rlog_len;
+  unsigned int _p3[27];
+  unsigned long long t_round[4];  // CTA 0's %globaltimer at the start of round r (ring)
+  unsigned long long t_work[4];   // ... when CTA 0 finished the work of round r
+  unsigned long long t_flush[4];  // ... when CTA 0 finished flushing round r
+  unsigned long long stats[4];    // edges inspected, in-edges pushed, candidates, live swept
+  RoundStat rs[4];
+  // segmented runs: a kernel that lacks the variant its scheduler picked saves
+  // the schedule state here and exits; the kernel that has it resumes from it
+  unsigned int resume;            // 1: a segment ended early, state in `saved`
+  unsigned int resume_variant;    // the variant the next segment must run
+  unsigned int segments;          // kernels run so far in this run
+  unsigned int _p5;
+  Sched saved;
 };
 
 struct Dev {
@@ -104,6 +111,8 @@ struct Dev {
   uint32_t* chunk_first;  // [c]: work-list entry that owns edge 32c of the prefix
   uint32_t* bsum;     // per-CTA scratch of the grid-wide scan
   uint32_t sbuf_cap;  // entries of each CTA append buffer (dynamic shared memory)
+  uint32_t resume;    // 1: continue the run from Ctrl::saved instead of starting it
+  uint32_t bar_base;  // grid-barrier counter when this kernel starts (0 for a new run)
   Ctrl* C;
   trim_round_rec_t* rlog;
   uint32_t rlog_cap;
@@ -174,6 +183,9 @@ __device__ __forceinline__ void set_error(const Dev& D, unsigned code, unsigned 
 __global__ void trim_persistent_kernel_m1(trimk::Dev D);   // AC-4 only
 __global__ void trim_persistent_kernel_m2(trimk::Dev D);   // AC-6 only
 __global__ void trim_persistent_kernel_m4(trimk::Dev D);   // AC-3 only
+__global__ void trim_persistent_kernel_m9(trimk::Dev D);   // AC-4 + schedulers (segments)
+__global__ void trim_persistent_kernel_m10(trimk::Dev D);  // AC-6 + schedulers (segments)
+__global__ void trim_persistent_kernel_m12(trimk::Dev D);  // AC-3 + schedulers (segments)
 __global__ void trim_persistent_kernel_m15(trimk::Dev D);  // all variants + schedulers
 __global__ void trim_reset_ctrl_kernel(trimk::Ctrl* C);
 __global__ void trim_status_kernel(const uint32_t* level, uint32_t n, uint8_t* status);

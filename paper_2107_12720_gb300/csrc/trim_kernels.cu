@@ -89,7 +89,8 @@ struct Cta {
 #endif
   Sched S;
   WarpSlice ws[MAX_WARPS];
-  unsigned epoch;  // grid barriers passed
+  unsigned epoch;     // grid barriers passed by this kernel
+  unsigned bar_base;  // barrier counter when this kernel started
   unsigned err;
   uint32_t wbuf[MAX_WARPS][WBUF];
 };
@@ -179,13 +180,15 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   const unsigned mask = __ballot_sync(FULL, pred);
   if (mask == 0u) return;
   const bool feats = (MODES & M_SCHED) && (D.flags & F_NEED_FEATURES);
-  const bool track = D.ioff != nullptr && (((MODES & M_AC4) && (D.flags & F_AC4_POSSIBLE)) || feats);
+  // every flavour that may hand the run to AC-4 keeps its work list complete
+  constexpr bool may4 = (MODES & (M_AC4 | M_SCHED)) != 0;
+  const bool track = D.ioff != nullptr && ((may4 && (D.flags & F_AC4_POSSIBLE)) || feats);
   uint32_t row = 0, din = 0;
   if (pred && track) {
     row = __ldg(&D.ioff[u]);
     din = __ldg(&D.ioff[u + 1]) - row;
   }
-  const bool w = (MODES & M_AC4) && pred && din > 0u && (D.flags & F_AC4_POSSIBLE);
+  const bool w = may4 && pred && din > 0u && (D.flags & F_AC4_POSSIBLE);
   const unsigned wmask = __ballot_sync(FULL, w);
   const unsigned lt = (1u << lane) - 1u;
   const unsigned k = __popc(mask), kw = __popc(wmask);
@@ -249,7 +252,8 @@ __device__ __forceinline__ void append_live(const Dev& D, Cta& B, bool pred, uin
 }
 
 // End of round r: moves every warp slice of the CTA to global memory with one
-// global atomic per counter (all threads of the CTA).
+// global atomic per counter (all threads of the CTA). The (up to three) space
+// reservations are issued by three lanes at once, so they cost one round trip.
 __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out) {
   __syncthreads();
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -257,44 +261,44 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
     // exclusive prefix of the per-warp counts (lane i holds warp i)
     const bool has = lane < nw;
     const uint32_t a = has ? B.ws[lane].nlog + B.ws[lane].ncount : 0u,
-                   b = has ? B.ws[lane].nw4 : 0u,
-                   c = has ? B.ws[lane].nedge : 0u, d = has ? B.ws[lane].nlive : 0u;
+                   b = has ? B.ws[lane].nw4 : 0u, c = has ? B.ws[lane].nedge : 0u,
+                   d = has ? B.ws[lane].nlive : 0u;
     const uint32_t ia = warp_incl_scan(a), ib = warp_incl_scan(b), ic = warp_incl_scan(c),
                    id = warp_incl_scan(d);
     const uint32_t ta = __shfl_sync(FULL, ia, 31), tb = __shfl_sync(FULL, ib, 31),
                    tc = __shfl_sync(FULL, ic, 31), td = __shfl_sync(FULL, id, 31);
-    unsigned long long s_in = has ? B.ws[lane].sum_in : 0ull;
-    unsigned long long s_out = has ? B.ws[lane].sum_out : 0ull;
-    uint32_t h[3];
-    for (int i = 0; i < 3; ++i) h[i] = warp_sum(has ? B.ws[lane].hist[i] : 0u);
-    s_in = warp_sum(s_in);
-    s_out = warp_sum(s_out);
-    uint32_t lb = 0, wb = 0, eb = 0, vb = 0;
-    if (lane == 0) {
-      RoundStat* rs = &D.C->rs[r & 3];
-      if (ta) {
-        lb = atomicAdd(&D.C->log_len, ta);
-        if (lb + ta > D.n) { set_error(D, TRIM_ERR_STATE, 0xD5); lb = 0xFFFFFFFFu; }
-      }
-      if (tb) {
-        const unsigned long long o =
-            atomicAdd(&D.C->w4, (unsigned long long)tb | ((unsigned long long)tc << 32));
-        wb = (uint32_t)o;
-        eb = (uint32_t)(o >> 32);
-      }
-      if (td) {
-        vb = atomicAdd(&rs->live_count, td);
-        if (vb + td > D.n) { set_error(D, TRIM_ERR_STATE, 0xD6); vb = 0xFFFFFFFFu; }
-      }
-      if (s_in) atomicAdd(&rs->sum_in, s_in);
-      if (s_out) atomicAdd(&rs->sum_out, s_out);
-      for (int i = 0; i < 3; ++i)
-        if (h[i]) atomicAdd(&rs->hist[i], h[i]);
+    RoundStat* rs = &D.C->rs[r & 3];
+    unsigned long long got = 0;
+    if (lane == 0 && ta) got = atomicAdd(&D.C->log_len, ta);
+    if (lane == 1 && tb)
+      got = atomicAdd(&D.C->w4, (unsigned long long)tb | ((unsigned long long)tc << 32));
+    if (lane == 2 && td) got = atomicAdd(&rs->live_count, td);
+    uint32_t lb = (uint32_t)__shfl_sync(FULL, got, 0);
+    const unsigned long long w4o = __shfl_sync(FULL, got, 1);
+    uint32_t vb = (uint32_t)__shfl_sync(FULL, got, 2);
+    const uint32_t wb = (uint32_t)w4o, eb = (uint32_t)(w4o >> 32);
+    if (ta && lb + ta > D.n) {
+      if (lane == 0) set_error(D, TRIM_ERR_STATE, 0xD5);
+      lb = 0xFFFFFFFFu;
     }
-    lb = __shfl_sync(FULL, lb, 0);
-    wb = __shfl_sync(FULL, wb, 0);
-    eb = __shfl_sync(FULL, eb, 0);
-    vb = __shfl_sync(FULL, vb, 0);
+    if (td && vb + td > D.n) {
+      if (lane == 0) set_error(D, TRIM_ERR_STATE, 0xD6);
+      vb = 0xFFFFFFFFu;
+    }
+    if ((MODES & M_SCHED) && (D.flags & F_NEED_FEATURES)) {
+      unsigned long long s_in = has ? B.ws[lane].sum_in : 0ull;
+      unsigned long long s_out = has ? B.ws[lane].sum_out : 0ull;
+      uint32_t h[3];
+      for (int i = 0; i < 3; ++i) h[i] = warp_sum(has ? B.ws[lane].hist[i] : 0u);
+      s_in = warp_sum(s_in);
+      s_out = warp_sum(s_out);
+      if (lane == 0) {
+        if (s_in) atomicAdd(&rs->sum_in, s_in);
+        if (s_out) atomicAdd(&rs->sum_out, s_out);
+        for (int i = 0; i < 3; ++i)
+          if (h[i]) atomicAdd(&rs->hist[i], h[i]);
+      }
+    }
     if (has) {
       WarpSlice& w = B.ws[lane];
       w.log_base = lb + ia - a;
@@ -320,13 +324,14 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
 // ------------------------------------------------------------------ grid barrier
 
 // Grid-wide barrier: each CTA adds one arrival to a monotone counter and waits
-// until all gridDim.x arrivals of this epoch are in. The wait is bounded by
-// spin_limit_ns; past it the run stops with TRIM_ERR_TIMEOUT. Returns false if
-// the run must stop (any error flag).
+// until all gridDim.x arrivals of this epoch are in (counted from the value the
+// counter had when this kernel started: a resumed segment continues it). The
+// wait is bounded by spin_limit_ns; past it the run stops with
+// TRIM_ERR_TIMEOUT. Returns false if the run must stop (any error flag).
 __device__ bool grid_barrier(const Dev& D, Cta& B) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned target = (++B.epoch) * gridDim.x;
+    const unsigned target = B.bar_base + (++B.epoch) * gridDim.x;
     fence_acq_rel();
     red_relaxed_add(&D.C->bar, 1u);
     const uint64_t t0 = globaltimer();
@@ -948,6 +953,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
   const uint32_t gwarp = blockIdx.x * wpb + (threadIdx.x >> 5);
   if (threadIdx.x == 0) {
     Sched& S = B.S;
+    B.bar_base = D.bar_base;
     S.round = 0; S.fb = 0; S.fe = 0;
     S.variant = NIL; S.prev_variant = NIL;
     S.c4w = 0; S.e_c4 = 0; S.w_end = 0; S.e_end = 0;
@@ -976,16 +982,46 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
       B.model[dst] = __ldg(&D.model[i]);
     }
 #endif
+  if (D.resume && threadIdx.x == 0) {
+    // continue a run that an earlier segment left at the start of round saved.round
+    const volatile uint32_t* w = reinterpret_cast<const volatile uint32_t*>(&D.C->saved);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&B.S);
+    for (unsigned i = 0; i < sizeof(Sched) / 4; ++i) dst[i] = w[i];
+  }
   __syncthreads();
-  start_round(D, 0);
-  init_round(D, B, gwarp, nwarps);
-  flush_round(D, B, 0, D.live0);
-  bool ok = grid_barrier(D, B);
+  bool ok = true;
+  if (!D.resume) {
+    start_round(D, 0);
+    init_round(D, B, gwarp, nwarps);
+    flush_round(D, B, 0, D.live0);
+    ok = grid_barrier(D, B);
+  }
+  bool fresh = !D.resume;  // a resumed segment starts with its round already chosen
   while (ok) {
-    if (threadIdx.x < 32) advance(D, B);
+    if (fresh && threadIdx.x < 32) advance(D, B);
+    fresh = true;
     __syncthreads();
     const Sched& S = B.S;  // changes only in advance(), between barriers
-    if (S.done) break;
+    if (S.done) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) D.C->resume = 0;
+      break;
+    }
+    const bool have = (S.variant == TRIM_AC4_PUSH && (MODES & M_AC4)) ||
+                      (S.variant == TRIM_AC6_SUPPORT && (MODES & M_AC6)) ||
+                      (S.variant == TRIM_AC3_PULL && (MODES & M_AC3));
+    if (!have) {
+      // this kernel lacks the chosen variant: hand the run to the kernel that
+      // has it (every CTA took the same decision, so all stop here)
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        volatile uint32_t* w = reinterpret_cast<volatile uint32_t*>(&D.C->saved);
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&B.S);
+        for (unsigned i = 0; i < sizeof(Sched) / 4; ++i) w[i] = src[i];
+        D.C->resume_variant = S.variant;
+        __threadfence();
+        D.C->resume = 1;
+      }
+      break;
+    }
     start_round(D, S.round);
     if ((MODES & M_AC4) && S.variant == TRIM_AC4_PUSH) {
       ac4_round(D, B, S, gwarp, nwarps);

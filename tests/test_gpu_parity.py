@@ -134,6 +134,51 @@ def test_random_schedules_are_bit_identical():
                 check(t, lvl, st, alpha, f"scripted{list(sched)}", t.run("scripted"))
 
 
+def _script_segments(sched, alpha):
+    """Kernel launches of a segmented scripted run: one, plus one per change of
+    variant between consecutive rounds (round k runs sched[(k-1) % len])."""
+    v = [int(sched[(k - 1) % len(sched)]) for k in range(1, alpha + 1)]
+    return 1 + sum(1 for a, b in zip(v, v[1:]) if a != b), v
+
+
+def test_segmented_runs_match_single_launch():
+    """A scheduled trim_run runs as segments on the single-variant kernels; the
+    single all-variant launch of trim_run_async computes the same run. Both must
+    equal the oracle, run the scripted variant in every round, and the segmented
+    run must take exactly one launch per change of variant."""
+    P = _P()
+    rng = np.random.default_rng(17)
+    for i in [1, 2, 4]:
+        g = cfg.config_small(i)
+        lvl, st, alpha = oracle.peel(g.off, g.tgt)
+        off, tgt = dev_csr(g)
+        oi, ti = dev_csr_in(g)
+        with P.Trimmer(off, tgt, oi, ti, flags=P.TRIM_FLAG_ROUND_LOG) as t:
+            scheds = [[0, 1, 2], [2, 2, 0], [1]] + [
+                list(rng.integers(0, 3, size=int(rng.integers(1, 7)))) for _ in range(3)]
+            for sched in scheds:
+                t.set_schedule(sched)
+                want_segments, want_v = _script_segments(sched, alpha)
+                s = t.run("scripted")
+                check(t, lvl, st, alpha, f"segmented{sched}", s)
+                assert s["segments"] == want_segments, (i, sched, s["segments"], want_segments)
+                assert [r.variant for r in t.round_log()] == want_v
+                t.run_async("scripted")
+                s1 = t.sync()
+                check(t, lvl, st, alpha, f"single{sched}", s1)
+                assert s1["segments"] == 1
+                assert [r.variant for r in t.round_log()] == want_v
+            for mode in ["heuristic", "learned"]:
+                s = t.run(mode)
+                check(t, lvl, st, alpha, mode, s)
+                seg_v = [r.variant for r in t.round_log()]
+                assert s["segments"] == 1 + sum(1 for a, b in zip(seg_v, seg_v[1:]) if a != b) \
+                    or s["segments"] == 2 + sum(1 for a, b in zip(seg_v, seg_v[1:]) if a != b)
+                t.run_async(mode)
+                check(t, lvl, st, alpha, mode + "-single", t.sync())
+                assert [r.variant for r in t.round_log()] == seg_v
+
+
 def test_random_graphs_with_duplicates_and_loops():
     P = _P()
     rng = np.random.default_rng(11)
@@ -259,3 +304,27 @@ def test_full_batched_workload():
     with P.Trimmer(off, tgt) as t:
         for v in ["ac4", "heuristic"]:
             check(t, lvl, st, alpha, f"batch-{v}", t.batch_run(u.graph_off, v))
+
+
+def test_full_large_mixed_workload_certificate():
+    """The large mixed workload at full size (R-MAT scale 26 union a 2^25-vertex
+    planted block: n = 100.7M, m = 1.22e9, alpha = 10,004) in the launch shape the
+    benchmark uses. Checked with the oracle's certificate, which holds for exactly
+    one status/level assignment (the trimming result), plus the planted block's
+    closed form (C and R live, chain vertices at their chain position)."""
+    P = _P()
+    u = cfg.config(4)
+    off, tgt = dev_csr(u)
+    rmat_n = u.meta["rmat_n"]
+    nC, nR, nT, chains = u.meta["block"]
+    with P.Trimmer(off, tgt) as t:
+        for v in ["ac4", "heuristic"]:
+            s = t.run(v)
+            lvl = t.level(device=False)
+            st = t.status(device=False)
+            assert oracle.certificate(u.off, u.tgt, lvl, st) == -1, v
+            blk = lvl[rmat_n:]
+            assert (blk[:nC + nR] == P.TRIM_LIVE).all()
+            np.testing.assert_array_equal(blk[nC + nR:], np.arange(nT, dtype=np.uint32) // chains)
+            assert s["rounds"] == int(lvl[lvl != P.TRIM_LIVE].max()) + 1
+        del lvl, st
