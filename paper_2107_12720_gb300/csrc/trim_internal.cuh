@@ -56,6 +56,7 @@ struct Sched {
   uint32_t done;
   uint32_t fprev;         // frontier size of round r-1 (timing feature)
   uint32_t mixed;         // 1 once a round ran AC-6 or AC-3 (AC-4 must then re-check levels)
+  uint32_t vcount[3];     // rounds run so far by AC-4, AC-6, AC-3
   unsigned long long m_live;     // out-edges of live vertices
   float feat[12];                // features that chose this round's variant
 };

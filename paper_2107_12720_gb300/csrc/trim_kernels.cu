@@ -78,7 +78,7 @@ struct WarpSlice {
   uint32_t nlog, nw4, nedge, nlive;   // entries in the slices; edges of the w4 entries
   uint32_t ncount;                    // removals counted in the log but not written to it
   uint32_t log_base, w4_base, edge_base, live_base;  // global bases at the CTA flush
-  unsigned long long sum_in, sum_out;
+  uint32_t sum_in, sum_out;  // feature sums (distinct removed vertices: at most m < 2^32)
   uint32_t hist[3];
 };
 
@@ -183,11 +183,12 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   // every flavour that may hand the run to AC-4 keeps its work list complete
   constexpr bool may4 = (MODES & (M_AC4 | M_SCHED)) != 0;
   const bool track = D.ioff != nullptr && ((may4 && (D.flags & F_AC4_POSSIBLE)) || feats);
-  uint32_t row = 0, din = 0;
+  uint32_t row = 0, din = 0, dout = 0;
   if (pred && track) {
     row = __ldg(&D.ioff[u]);
     din = __ldg(&D.ioff[u + 1]) - row;
   }
+  if (pred && feats) dout = __ldg(&D.off[u + 1]) - __ldg(&D.off[u]);
   const bool w = may4 && pred && din > 0u && (D.flags & F_AC4_POSSIBLE);
   const unsigned wmask = __ballot_sync(FULL, w);
   const unsigned lt = (1u << lane) - 1u;
@@ -208,13 +209,11 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
     slice(warp, 1)[at] = row;
     slice(warp, 2)[at] = pe + eincl - ew;
   }
-  unsigned long long s_in = 0, s_out = 0;
+  unsigned s_in = 0, s_out = 0;
   unsigned h0 = 0, h1 = 0;
   if (feats) {
-    unsigned dout = 0;
-    if (pred) dout = __ldg(&D.off[u + 1]) - __ldg(&D.off[u]);
-    s_out = warp_sum<unsigned long long>(dout);
-    s_in = warp_sum<unsigned long long>(din);
+    s_out = __reduce_add_sync(FULL, dout);
+    s_in = __reduce_add_sync(FULL, din);
     h0 = __popc(__ballot_sync(FULL, pred && din < 8u));
     h1 = __popc(__ballot_sync(FULL, pred && din >= 8u && din < 256u));
   }
@@ -286,18 +285,14 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
       vb = 0xFFFFFFFFu;
     }
     if ((MODES & M_SCHED) && (D.flags & F_NEED_FEATURES)) {
-      unsigned long long s_in = has ? B.ws[lane].sum_in : 0ull;
-      unsigned long long s_out = has ? B.ws[lane].sum_out : 0ull;
+      const uint32_t s_in = __reduce_add_sync(FULL, has ? B.ws[lane].sum_in : 0u);
+      const uint32_t s_out = __reduce_add_sync(FULL, has ? B.ws[lane].sum_out : 0u);
       uint32_t h[3];
-      for (int i = 0; i < 3; ++i) h[i] = warp_sum(has ? B.ws[lane].hist[i] : 0u);
-      s_in = warp_sum(s_in);
-      s_out = warp_sum(s_out);
-      if (lane == 0) {
-        if (s_in) atomicAdd(&rs->sum_in, s_in);
-        if (s_out) atomicAdd(&rs->sum_out, s_out);
-        for (int i = 0; i < 3; ++i)
-          if (h[i]) atomicAdd(&rs->hist[i], h[i]);
-      }
+      for (int i = 0; i < 3; ++i) h[i] = __reduce_add_sync(FULL, has ? B.ws[lane].hist[i] : 0u);
+      // five lanes, five independent reductions (no return value: no wait)
+      if (lane == 3 && s_in) atomicAdd(&rs->sum_in, (unsigned long long)s_in);
+      if (lane == 4 && s_out) atomicAdd(&rs->sum_out, (unsigned long long)s_out);
+      if (lane >= 5 && lane < 8 && h[lane - 5]) atomicAdd(&rs->hist[lane - 5], h[lane - 5]);
     }
     if (has) {
       WarpSlice& w = B.ws[lane];
@@ -328,7 +323,9 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
 // counter had when this kernel started: a resumed segment continues it). The
 // wait is bounded by spin_limit_ns; past it the run stops with
 // TRIM_ERR_TIMEOUT. Returns false if the run must stop (any error flag).
-__device__ bool grid_barrier(const Dev& D, Cta& B) {
+// With read_err false the error flag is not read here: the round loop reads it
+// in advance(), together with the round's counters (one memory round trip less).
+__device__ bool grid_barrier(const Dev& D, Cta& B, bool read_err = true) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned target = B.bar_base + (++B.epoch) * gridDim.x;
@@ -338,10 +335,11 @@ __device__ bool grid_barrier(const Dev& D, Cta& B) {
     while ((int)(ld_acquire(&D.C->bar) - target) < 0) {
       if (globaltimer() - t0 > D.spin_limit_ns) {
         set_error(D, TRIM_ERR_TIMEOUT, 1);
+        B.err = TRIM_ERR_TIMEOUT;
         break;
       }
     }
-    B.err = ld_relaxed(&D.C->err);
+    if (read_err) B.err = ld_relaxed(&D.C->err);
   }
   __syncthreads();
   return B.err == 0u;
@@ -484,10 +482,11 @@ __device__ uint32_t mlp_choice(const Dev& D, const float* B, const float* f, boo
 #pragma unroll
   for (int i = 0; i < NFEAT; ++i) h1 = fmaf(W1t[i * 32 + lane], x[i], h1);
   h1 = fmaxf(h1, 0.0f);
-  float h2 = b2[lane];
+  float acc[4] = {b2[lane], 0.0f, 0.0f, 0.0f};  // four chains for instruction-level parallelism
 #pragma unroll
-  for (int k = 0; k < 32; ++k) h2 = fmaf(W2t[k * 32 + lane], __shfl_sync(FULL, h1, k), h2);
-  h2 = fmaxf(h2, 0.0f);
+  for (int k = 0; k < 32; ++k)
+    acc[k & 3] = fmaf(W2t[k * 32 + lane], __shfl_sync(FULL, h1, k), acc[k & 3]);
+  const float h2 = fmaxf((acc[0] + acc[1]) + (acc[2] + acc[3]), 0.0f);
   float z[3];
 #pragma unroll
   for (int o = 0; o < 3; ++o) z[o] = warp_sum(W3[o * 32 + lane] * h2) + b3[o];
@@ -511,23 +510,38 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
   Sched L = B.S;
   const uint32_t r = L.round;
   const RoundStat* rs = &C->rs[r & 3];
+  const bool feats = (MODES & M_SCHED) && (D.flags & F_NEED_FEATURES);
+  const bool logged = (D.flags & F_ROUND_LOG) && D.rlog != nullptr && r >= 1 && r - 1 < D.rlog_cap;
+  // every value this step reads from the control block, issued together
+  const uint32_t err = ld_relaxed(&C->err);
   const uint32_t len = ld_relaxed(&C->log_len);
   const unsigned long long w4 = ld_relaxed64(&C->w4);
   const uint32_t live_count = ld_relaxed(&rs->live_count);
+  unsigned long long sum_in = 0, sum_out = 0, t_r = 0, t_rm1 = 0;
+  uint32_t h0 = 0, h1 = 0, h2 = 0;
+  if (feats) {
+    sum_in = ld_relaxed64(&rs->sum_in);
+    sum_out = ld_relaxed64(&rs->sum_out);
+    h0 = ld_relaxed(&rs->hist[0]);
+    h1 = ld_relaxed(&rs->hist[1]);
+    h2 = ld_relaxed(&rs->hist[2]);
+    t_rm1 = ld_relaxed64(&C->t_round[(r - 1) & 3]);
+  }
+  if (feats || logged) t_r = ld_relaxed64(&C->t_round[r & 3]);
   const uint32_t w_end = (uint32_t)w4, e_end = (uint32_t)(w4 >> 32);
   const uint32_t nF = len - L.fe;  // |F_r|
-  const bool feats = (MODES & M_SCHED) && (D.flags & F_NEED_FEATURES);
   const bool cta0 = blockIdx.x == 0 && lane == 0;
   if (r >= 1) {
+    if (L.variant <= 2u) L.vcount[L.variant] += 1;
     if (cta0) {
-      if (L.variant <= 2u) C->vcount[L.variant] += 1;
-      if ((D.flags & F_ROUND_LOG) && D.rlog != nullptr && r - 1 < D.rlog_cap) {
+      if (L.variant <= 2u) C->vcount[L.variant] = L.vcount[L.variant];
+      if (logged) {
         trim_round_rec_t* rec = &D.rlog[r - 1];
         rec->round = r;
         rec->variant = L.variant;
         rec->frontier = L.fe - L.fb;
         rec->removed = nF;
-        rec->t_start_ns = ld_relaxed64(&C->t_round[r & 3]);
+        rec->t_start_ns = t_r;
         rec->t_end_ns = globaltimer();
         rec->t_work_ns = ld_relaxed64(&C->t_work[r & 3]);
         rec->t_flush_ns = ld_relaxed64(&C->t_flush[r & 3]);
@@ -556,12 +570,6 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
     float f[NFEAT];
     for (int i = 0; i < NFEAT; ++i) f[i] = 0.0f;
     if (feats) {
-      const unsigned long long sum_in = ld_relaxed64(&rs->sum_in);
-      const unsigned long long sum_out = ld_relaxed64(&rs->sum_out);
-      const uint32_t h0 = ld_relaxed(&rs->hist[0]), h1 = ld_relaxed(&rs->hist[1]),
-                     h2 = ld_relaxed(&rs->hist[2]);
-      const unsigned long long t_r = ld_relaxed64(&C->t_round[r & 3]);
-      const unsigned long long t_rm1 = ld_relaxed64(&C->t_round[(r - 1) & 3]);
       L.m_live -= sum_out;
       f[0] = log2p1((float)nF);
       f[1] = log2p1((float)sum_in);
@@ -609,7 +617,10 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
     for (int i = 0; i < NFEAT; ++i) L.feat[i] = f[i];
   }
   __syncwarp();
-  if (lane == 0) B.S = L;
+  if (lane == 0) {
+    B.S = L;
+    B.err = err;
+  }
 }
 
 // CTA 0, start of round k: timestamp, and zero the accumulator slot of round k+2.
@@ -959,6 +970,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     S.c4w = 0; S.e_c4 = 0; S.w_end = 0; S.e_end = 0;
     S.ac3_list = NIL; S.live_in_len = 0; S.live_out = 0;
     S.done = 0; S.fprev = 0; S.mixed = 0;
+    S.vcount[0] = S.vcount[1] = S.vcount[2] = 0;
     S.m_live = D.m;
     for (int i = 0; i < NFEAT; ++i) S.feat[i] = 0.0f;
 
@@ -994,13 +1006,14 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     start_round(D, 0);
     init_round(D, B, gwarp, nwarps);
     flush_round(D, B, 0, D.live0);
-    ok = grid_barrier(D, B);
+    ok = grid_barrier(D, B, false);
   }
   bool fresh = !D.resume;  // a resumed segment starts with its round already chosen
   while (ok) {
-    if (fresh && threadIdx.x < 32) advance(D, B);
+    if (fresh && threadIdx.x < 32) advance(D, B);  // also reads the error flag
     fresh = true;
     __syncthreads();
+    if (B.err) break;
     const Sched& S = B.S;  // changes only in advance(), between barriers
     if (S.done) {
       if (blockIdx.x == 0 && threadIdx.x == 0) D.C->resume = 0;
@@ -1034,7 +1047,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     if (stamp) D.C->t_work[S.round & 3] = globaltimer();
     flush_round(D, B, S.round, S.live_out ? D.live1 : D.live0);
     if (stamp) D.C->t_flush[S.round & 3] = globaltimer();
-    ok = grid_barrier(D, B);
+    ok = grid_barrier(D, B, false);
   }
 }
 
