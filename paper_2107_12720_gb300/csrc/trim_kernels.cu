@@ -92,6 +92,7 @@ struct Cta {
   unsigned epoch;     // grid barriers passed by this kernel
   unsigned bar_base;  // barrier counter when this kernel started
   unsigned err;
+  unsigned w4_wide;   // initial pass: the work-list slices take all four buffers
   uint32_t wbuf[MAX_WARPS][WBUF];
 };
 
@@ -111,33 +112,60 @@ __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gp
 __device__ __forceinline__ void red_relaxed_add(unsigned* p, unsigned v) {
   asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
 
 // ------------------------------------------------------------------ appends
 
-// Writes the chunk-owner index for work-list entry `pos` covering edges [es, ee):
-// every chunk start 32c in that range is owned by this entry.
-__device__ __forceinline__ void mark_chunks(const Dev& D, uint32_t pos, uint32_t es, uint32_t ee) {
-  for (uint32_t c = (es + 31u) >> 5; (c << 5) < ee; ++c) D.chunk_first[c] = pos;
+// Warp-collective: writes the chunk-owner index of the work-list entries the
+// lanes hold: every chunk start 32c inside an entry's edge range [es, ee) is
+// owned by that entry (pos). An entry with at most two chunk starts marks them
+// itself; a longer one (a hub) is marked by the whole warp, so one lane never
+// serialises thousands of stores.
+__device__ __forceinline__ void mark_chunks(const Dev& D, bool has, uint32_t pos, uint32_t es,
+                                            uint32_t ee) {
+  const uint32_t c0 = (es + 31u) >> 5, c1 = (ee + 31u) >> 5;  // chunk starts in [es, ee)
+  const bool big = has && c1 > c0 + 2u;
+  if (has && !big) {
+    if (c0 < c1) D.chunk_first[c0] = pos;
+    if (c0 + 1u < c1) D.chunk_first[c0 + 1u] = pos;
+  }
+  unsigned bm = __ballot_sync(FULL, big);
+  while (bm) {
+    const int j = __ffs(bm) - 1;
+    bm &= bm - 1u;
+    const uint32_t p = __shfl_sync(FULL, pos, j), a = __shfl_sync(FULL, c0, j),
+                   z = __shfl_sync(FULL, c1, j);
+    for (uint32_t c = a + lane_id(); c < z; c += 32u) D.chunk_first[c] = p;
+  }
 }
 
+// AC-4 work-list slices of a warp: G^T row starts and in-edge offsets. The
+// initial pass writes no dead log and no live list, so there they span two
+// buffers each (rows over buffers 0-1, offsets over 2-3): fewer warp flushes.
+__device__ __forceinline__ uint32_t* w4_rows(const Cta& B, unsigned warp) {
+  return slice(warp, B.w4_wide ? 0 : 1);
+}
+__device__ __forceinline__ uint32_t w4_cap(const Cta& B) { return B.w4_wide ? 2u * LW : LW; }
+
 // Warp-collective: copies this warp's slices to global memory at the given bases.
-__device__ __forceinline__ void copy_slices(const Dev& D, const WarpSlice& w, unsigned warp,
-                                            uint32_t* live_out) {
+__device__ __forceinline__ void copy_slices(const Dev& D, const Cta& B, const WarpSlice& w,
+                                            unsigned warp, uint32_t* live_out) {
   const unsigned lane = lane_id();
   const uint32_t* sl = slice(warp, 0);
-  const uint32_t* sr = slice(warp, 1);
+  const uint32_t* sr = w4_rows(B, warp);
   const uint32_t* se = slice(warp, 2);
   const uint32_t* sv = slice(warp, 3);
   for (uint32_t i = lane; i < w.nlog; i += 32) D.log[w.log_base + i] = sl[i];
-  for (uint32_t i = lane; i < w.nw4; i += 32) {
-    const uint32_t eo = w.edge_base + se[i];
-    const uint32_t ee = w.edge_base + (i + 1 < w.nw4 ? se[i + 1] : w.nedge);
-    D.w4_row[w.w4_base + i] = sr[i];
-    D.w4_eoff[w.w4_base + i] = eo;
-    mark_chunks(D, w.w4_base + i, eo, ee);
+  for (uint32_t i0 = 0; i0 < w.nw4; i0 += 32) {  // warp-uniform loop: mark_chunks is collective
+    const uint32_t i = i0 + lane;
+    const bool has = i < w.nw4;
+    uint32_t eo = 0, ee = 0;
+    if (has) {
+      eo = w.edge_base + se[i];
+      ee = w.edge_base + (i + 1 < w.nw4 ? se[i + 1] : w.nedge);
+      D.w4_row[w.w4_base + i] = sr[i];
+      D.w4_eoff[w.w4_base + i] = eo;
+    }
+    mark_chunks(D, has, w.w4_base + i, eo, ee);
   }
   for (uint32_t i = lane; i < w.nlive; i += 32) live_out[w.live_base + i] = sv[i];
 }
@@ -146,36 +174,39 @@ __device__ __forceinline__ void copy_slices(const Dev& D, const WarpSlice& w, un
 __device__ __noinline__ void warp_flush(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out) {
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   WarpSlice& w = B.ws[warp];
-  if (lane == 0) {
-    if (w.nlog + w.ncount) {
-      w.log_base = atomicAdd(&D.C->log_len, w.nlog + w.ncount);
-      if (w.log_base + w.nlog + w.ncount > D.n) { set_error(D, TRIM_ERR_STATE, 0xD1); w.nlog = 0; }
-    }
-    if (w.nw4) {
-      const unsigned long long o = atomicAdd(
-          &D.C->w4, (unsigned long long)w.nw4 | ((unsigned long long)w.nedge << 32));
-      w.w4_base = (uint32_t)o;
-      w.edge_base = (uint32_t)(o >> 32);
-    }
-    if (w.nlive) {
-      w.live_base = atomicAdd(&D.C->rs[r & 3].live_count, w.nlive);
-      if (w.live_base + w.nlive > D.n) { set_error(D, TRIM_ERR_STATE, 0xD3); w.nlive = 0; }
-    }
+  // three lanes reserve at once; removals that are only counted (nlog = 0)
+  // wait for the CTA flush
+  if (lane == 0 && w.nlog) {
+    w.log_base = atomicAdd(&D.C->log_len, w.nlog + w.ncount);
+    if (w.log_base + w.nlog + w.ncount > D.n) { set_error(D, TRIM_ERR_STATE, 0xD1); w.nlog = 0; }
+    w.ncount = 0;
+  }
+  if (lane == 1 && w.nw4) {
+    const unsigned long long o = atomicAdd(
+        &D.C->w4, (unsigned long long)w.nw4 | ((unsigned long long)w.nedge << 32));
+    w.w4_base = (uint32_t)o;
+    w.edge_base = (uint32_t)(o >> 32);
+  }
+  if (lane == 2 && w.nlive) {
+    w.live_base = atomicAdd(&D.C->rs[r & 3].live_count, w.nlive);
+    if (w.live_base + w.nlive > D.n) { set_error(D, TRIM_ERR_STATE, 0xD3); w.nlive = 0; }
   }
   __syncwarp();
   const WarpSlice c = w;
-  copy_slices(D, c, warp, live_out);
+  copy_slices(D, B, c, warp, live_out);
   __syncwarp();
-  if (lane == 0) w.nlog = w.nw4 = w.nedge = w.nlive = w.ncount = 0;
+  if (lane == 0) w.nlog = w.nw4 = w.nedge = w.nlive = 0;
   __syncwarp();
 }
 
 // Warp-collective: lanes with pred are removed in round r: level[u] = r and u
 // joins F_r in the dead log; if it has in-edges (and AC-4 may run) it also
-// joins the AC-4 work list with its G^T row and in-degree.
+// joins the AC-4 work list with its G^T row and in-degree. With pre, the caller
+// has already loaded u's G^T row start (prow) and in-degree (pdin).
 __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uint32_t u,
                                             uint32_t r, uint32_t* live_out,
-                                            bool initial = false) {
+                                            bool initial = false, bool pre = false,
+                                            uint32_t prow = 0, uint32_t pdin = 0) {
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned mask = __ballot_sync(FULL, pred);
   if (mask == 0u) return;
@@ -185,10 +216,16 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   const bool track = D.ioff != nullptr && ((may4 && (D.flags & F_AC4_POSSIBLE)) || feats);
   uint32_t row = 0, din = 0, dout = 0;
   if (pred && track) {
-    row = __ldg(&D.ioff[u]);
-    din = __ldg(&D.ioff[u + 1]) - row;
+    if (pre) {
+      row = prow;
+      din = pdin;
+    } else {
+      row = __ldg(&D.ioff[u]);
+      din = __ldg(&D.ioff[u + 1]) - row;
+    }
   }
-  if (pred && feats) dout = __ldg(&D.off[u + 1]) - __ldg(&D.off[u]);
+  // F_0 holds the vertices without out-edges
+  if (pred && feats && !initial) dout = __ldg(&D.off[u + 1]) - __ldg(&D.off[u]);
   const bool w = may4 && pred && din > 0u && (D.flags & F_AC4_POSSIBLE);
   const unsigned wmask = __ballot_sync(FULL, w);
   const unsigned lt = (1u << lane) - 1u;
@@ -198,7 +235,7 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   const unsigned esum = __shfl_sync(FULL, eincl, 31);
   WarpSlice& ws = B.ws[warp];
   const unsigned kl = initial ? 0u : k;  // F_0 is only counted: no variant reads it back
-  if (ws.nlog + kl > LW || ws.nw4 + kw > LW) warp_flush(D, B, r, live_out);
+  if (ws.nlog + kl > LW || ws.nw4 + kw > w4_cap(B)) warp_flush(D, B, r, live_out);
   const uint32_t pl = ws.nlog, pw = ws.nw4, pe = ws.nedge;
   if (pred && !initial) {
     slice(warp, 0)[pl + __popc(mask & lt)] = u;
@@ -206,7 +243,7 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   }
   if (w) {
     const unsigned at = pw + __popc(wmask & lt);
-    slice(warp, 1)[at] = row;
+    w4_rows(B, warp)[at] = row;
     slice(warp, 2)[at] = pe + eincl - ew;
   }
   unsigned s_in = 0, s_out = 0;
@@ -306,7 +343,7 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
   }
   __syncthreads();
   const WarpSlice c = B.ws[warp];
-  copy_slices(D, c, warp, live_out);
+  copy_slices(D, B, c, warp, live_out);
   __syncwarp();
   if (lane == 0) {
     WarpSlice& w = B.ws[warp];
@@ -655,13 +692,15 @@ __device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_
   const uint32_t c0 = ea >> 5, c1 = (eb + 31u) >> 5;
   const uint32_t per = (c1 - c0 + nwarps - 1) / nwarps;
   const uint32_t cb = c0 + gwarp * per, ce = min(c1, cb + per);
+  uint32_t cfb = 0;
   for (uint32_t c = cb; c < ce; c += U) {
-    const uint32_t cf = (lane < (unsigned)U && c + lane < ce) ? ldcg(&D.chunk_first[c + lane]) : 0u;
+    const uint32_t k = (c - cb) & 31u;
+    if (k == 0u) cfb = (c + lane < ce) ? ldcg(&D.chunk_first[c + lane]) : 0u;
     uint32_t wrow[U], weo[U], u[U], old[U];
     bool valid[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
-      const uint32_t first = max(__shfl_sync(FULL, cf, q), ia);
+      const uint32_t first = max(__shfl_sync(FULL, cfb, (k + q) & 31u), ia);
       const uint32_t ii = first + lane;
       const bool in = c + q < ce && ii < ib;
       wrow[q] = in ? ldcg(&D.w4_row[ii]) : 0u;
@@ -933,22 +972,39 @@ __device__ ROUND_FN bool ac6_round(const Dev& D, Cta& B, const Sched& S, uint32_
 
 // ------------------------------------------------------------------ init (round 0)
 
+// Each warp takes U blocks of 32 consecutive vertices at a time and issues all
+// their offset loads (and G^T offsets, needed for the sinks' work-list entries)
+// before using any: the pass is bound by memory parallelism, not by bandwidth.
 __device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32_t nwarps) {
+  constexpr int U = 4;
   const unsigned lane = lane_id();
   const uint32_t n = D.n;
   const bool w4 = (D.flags & F_AC4_POSSIBLE) != 0;
   const bool w6 = (D.flags & (F_AC6_POSSIBLE | F_AC3_POSSIBLE)) != 0;
-  for (uint32_t base = gwarp * 32; base < n; base += nwarps * 32) {
-    const uint32_t v = base + lane;
-    const bool has = v < n;
-    uint32_t d = 0;
-    if (has) {
-      d = __ldg(&D.off[v + 1]) - __ldg(&D.off[v]);
-      D.level[v] = d ? LIVE : 0u;
-      if (w4) D.cnt[v] = d;
-      if (w6) D.supp[v] = 0u;
+  const bool rows = D.ioff != nullptr;
+  for (uint32_t base = gwarp * (32u * U); base < n; base += nwarps * (32u * U)) {
+    uint32_t o0[U], o1[U], i0[U], i1[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const uint32_t v = base + q * 32u + lane;
+      const bool has = v < n;
+      o0[q] = has ? __ldg(&D.off[v]) : 0u;
+      o1[q] = has ? __ldg(&D.off[v + 1]) : 0u;
+      i0[q] = (has && rows) ? __ldg(&D.ioff[v]) : 0u;
+      i1[q] = (has && rows) ? __ldg(&D.ioff[v + 1]) : 0u;
     }
-    append_dead(D, B, has && d == 0u, v, 0u, D.live0, true);
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const uint32_t v = base + q * 32u + lane;
+      const bool has = v < n;
+      const uint32_t d = o1[q] - o0[q];
+      if (has) {
+        D.level[v] = d ? LIVE : 0u;
+        if (w4) D.cnt[v] = d;
+        if (w6) D.supp[v] = 0u;
+      }
+      append_dead(D, B, has && d == 0u, v, 0u, D.live0, true, true, i0[q], i1[q] - i0[q]);
+    }
   }
 }
 
@@ -982,6 +1038,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     }
     B.epoch = 0;
     B.err = 0;
+    B.w4_wide = 0;
   }
 #if TRIM_MODES & 8
   // blob layout W1[32][12] b1 W2[32][32] b2 W3[3][32] b3 mean istd lo hi; W1 and
@@ -1004,9 +1061,14 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
   bool ok = true;
   if (!D.resume) {
     start_round(D, 0);
+    if (threadIdx.x == 0) B.w4_wide = 1;
+    __syncthreads();
     init_round(D, B, gwarp, nwarps);
     flush_round(D, B, 0, D.live0);
     ok = grid_barrier(D, B, false);
+    // every warp's copy finished before the barrier; the __syncthreads after
+    // advance() publishes this before any work-list append
+    if (threadIdx.x == 0) B.w4_wide = 0;
   }
   bool fresh = !D.resume;  // a resumed segment starts with its round already chosen
   while (ok) {
