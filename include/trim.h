@@ -113,7 +113,17 @@ typedef struct {
 } trim_run_stats_t;
 
 /* One record per round of a TRIM_FLAG_ROUND_LOG run. features[] are the
- * scheduler inputs computed before the round (see trim_features_doc). */
+ * scheduler inputs computed before the round r, from round r-1 (F = F_{r-1}):
+ *   0 log2(1+|F|)            1 log2(1+sum of in-degrees of F)
+ *   2 log2(1+in-edges of removed vertices that AC-4 has not pushed yet)
+ *   3 log2(1+live vertices)  4 log2(1+live edges)   5 |F| / live vertices
+ *   6 sum of in-degrees of F / live edges
+ *   7..9 fractions of F with in-degree < 8, < 256, >= 256
+ *   10 log2(1 + ns per frontier vertex of round r-2)  11 variant of round r-1 (-1: none)
+ * Live edges: edges between live vertices when G^T is present, out-edges of
+ * live vertices without it; the in-degree features are 0 without G^T.
+ * Features are computed only for TRIM_SCHED_LEARNED runs and for scheduled
+ * runs with TRIM_FLAG_ROUND_LOG; otherwise they are 0. */
 typedef struct {
   uint32_t round;        /* r: the round that removes the vertices of level r          */
   uint32_t variant;      /* trim_variant_t actually run (0..2)                        */
@@ -121,8 +131,8 @@ typedef struct {
   uint32_t removed;      /* |F_r|                                                     */
   uint64_t t_start_ns;   /* device %globaltimer at the start of the round              */
   uint64_t t_end_ns;     /* ... at its end (after the grid-wide barrier)               */
-  uint64_t t_work_ns;    /* ... when the first CTA finished its share of the work     */
-  uint64_t t_flush_ns;   /* ... when the first CTA finished moving its buffers out    */
+  uint64_t t_work_ns;    /* ... when CTA 0 finished its share of the work              */
+  uint64_t t_flush_ns;   /* ... when CTA 0 finished moving its buffers out             */
   float features[12];
 } trim_round_rec_t;
 

@@ -202,11 +202,14 @@ __device__ __noinline__ void warp_flush(const Dev& D, Cta& B, uint32_t r, uint32
 // Warp-collective: lanes with pred are removed in round r: level[u] = r and u
 // joins F_r in the dead log; if it has in-edges (and AC-4 may run) it also
 // joins the AC-4 work list with its G^T row and in-degree. With pre, the caller
-// has already loaded u's G^T row start (prow) and in-degree (pdin).
+// has already loaded u's G^T row start (prow) and in-degree (pdin). dout is u's
+// out-degree where the caller knows it (AC-3/AC-6 scans; 0 for AC-4, which
+// never loads it): it only feeds the scheduler's live-edge count without G^T.
 __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uint32_t u,
                                             uint32_t r, uint32_t* live_out,
                                             bool initial = false, bool pre = false,
-                                            uint32_t prow = 0, uint32_t pdin = 0) {
+                                            uint32_t prow = 0, uint32_t pdin = 0,
+                                            uint32_t dout = 0) {
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned mask = __ballot_sync(FULL, pred);
   if (mask == 0u) return;
@@ -214,7 +217,8 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   // every flavour that may hand the run to AC-4 keeps its work list complete
   constexpr bool may4 = (MODES & (M_AC4 | M_SCHED)) != 0;
   const bool track = D.ioff != nullptr && ((may4 && (D.flags & F_AC4_POSSIBLE)) || feats);
-  uint32_t row = 0, din = 0, dout = 0;
+  uint32_t row = 0, din = 0;
+  if (!pred) dout = 0;
   if (pred && track) {
     if (pre) {
       row = prow;
@@ -224,8 +228,6 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
       din = __ldg(&D.ioff[u + 1]) - row;
     }
   }
-  // F_0 holds the vertices without out-edges
-  if (pred && feats && !initial) dout = __ldg(&D.off[u + 1]) - __ldg(&D.off[u]);
   const bool w = may4 && pred && din > 0u && (D.flags & F_AC4_POSSIBLE);
   const unsigned wmask = __ballot_sync(FULL, w);
   const unsigned lt = (1u << lane) - 1u;
@@ -607,10 +609,14 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
     float f[NFEAT];
     for (int i = 0; i < NFEAT; ++i) f[i] = 0.0f;
     if (feats) {
-      L.m_live -= sum_out;
+      // live-edge count. With G^T: edges between live vertices, i.e. m minus the
+      // in-edges of removed vertices (a removed vertex has only removed
+      // successors, so every edge that touches one ends in one). Without G^T:
+      // out-edges of live vertices (AC-3/AC-6 know each removed vertex's degree).
+      L.m_live -= (D.ioff != nullptr) ? sum_in : sum_out;
       f[0] = log2p1((float)nF);
       f[1] = log2p1((float)sum_in);
-      f[2] = log2p1((float)sum_out);
+      f[2] = log2p1((float)(e_end - L.e_c4));  // in-edges AC-4 has not pushed yet
       f[3] = log2p1((float)n_live);
       f[4] = log2p1((float)L.m_live);
       f[5] = (float)nF / (float)max(1u, n_live);
@@ -756,7 +762,7 @@ __device__ ROUND_FN void ac3_round(const Dev& D, Cta& B, const Sched& S, uint32_
     const bool stays = alive && !dies;
     if (stays && i != i0) D.supp[v] = i;
     K.swept += has ? 1 : 0;
-    append_dead(D, B, dies, v, r, Lout);
+    append_dead(D, B, dies, v, r, Lout, false, false, 0, 0, d);
     append_live(D, B, stays, v, r, Lout);
   }
   stats_flush(D, K);
@@ -785,7 +791,7 @@ __device__ __forceinline__ void ac6_rescan(const Dev& D, Cta& B, bool valid, uin
     D.s_next[v] = atomicExch(&D.s_head[t], v);
   }
   K.cand += valid ? 1 : 0;
-  append_dead(D, B, dies, v, r, D.live0);
+  append_dead(D, B, dies, v, r, D.live0, false, false, 0, 0, d);
 }
 
 // Block-wide exclusive scan of one value per thread (blockDim.x <= 1024).
@@ -857,7 +863,7 @@ __device__ ROUND_FN bool ac6_entry(const Dev& D, Cta& B, const Sched& S, uint32_
       atomicAdd(&D.s_cnt[t], 1u);
     }
     K.swept += has ? 1 : 0;
-    append_dead(D, B, dies, v, r, D.live0);
+    append_dead(D, B, dies, v, r, D.live0, false, false, 0, 0, d);
   }
   stats_flush(D, K);
   if (!grid_barrier(D, B)) return false;

@@ -16,11 +16,15 @@ it with the library's own CUDA kernels (trim_mlp_loss_grad, trim_mlp_adam_step):
                  the heuristic in the kernel).
 
 Feature vector of round r+1 (computed on the device after round r):
-  0 log2(1+|F_r|)   1 log2(1+sum indeg F_r)   2 log2(1+sum outdeg F_r)
+  0 log2(1+|F_r|)   1 log2(1+sum indeg F_r)
+  2 log2(1+in-edges of removed vertices that AC-4 has not pushed yet)
   3 log2(1+n_live)  4 log2(1+m_live)          5 |F_r| / n_live
   6 sum indeg F_r / m_live                    7..9 fractions of F_r with in-degree
   <8, <256, >=256   10 log2(1 + ns per frontier vertex of round r-1)
   11 the variant of round r (whose state is warm; -1 before round 1).
+m_live is the number of edges between live vertices when G^T is present (m
+minus the in-edges of removed vertices) and the number of out-edges of live
+vertices without it. The in-degree features are 0 without G^T.
 """
 from __future__ import annotations
 
@@ -31,7 +35,7 @@ import numpy as np
 from . import abi
 from .abi import TRIM_MLP_NIN, TRIM_MLP_NPARAMS
 
-FEATURES = ["log2_frontier", "log2_in_edges", "log2_out_edges", "log2_n_live", "log2_m_live",
+FEATURES = ["log2_frontier", "log2_in_edges", "log2_ac4_backlog", "log2_n_live", "log2_m_live",
             "frontier_over_live", "in_edges_over_m_live", "frac_indeg_lt8", "frac_indeg_lt256",
             "frac_indeg_ge256", "log2_ns_per_vertex_prev", "current_variant"]
 MODEL_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models")
