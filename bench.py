@@ -278,11 +278,18 @@ def time_variant(P, t, variant, steps, warmup, flush_buf, graph_off=None):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     last = None
+    # a scheduled variant runs as segments (trim_run: the host hands the run
+    # between single-variant kernels), a fixed one as one asynchronous launch
+    segmented = variant in ("heuristic", "learned", "scripted")
+    launches = 0
     for _ in range(steps):
         flush_buf.add_(1)  # writes more than the L2 holds, on the same stream
         e0.record(stream)
         if run:
             last = run()
+            e1.record(stream)
+        elif segmented:
+            last = t.run(variant)
             e1.record(stream)
         else:
             t.run_async(variant)
@@ -291,6 +298,8 @@ def time_variant(P, t, variant, steps, warmup, flush_buf, graph_off=None):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
         kern.append(last["device_ms"])
+        launches += 1 + last["segments"]  # control-block reset + persistent kernel(s)
+    last = dict(last, launches=launches)
     return times, kern, last
 
 
@@ -314,10 +323,12 @@ def per_graph_fixed(P, g, variant="ac4", limit=None):
     return total_ms * scale, count
 
 
-def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None):
-    """Through the C ABI with host buffers: trim_create copies the pinned host
-    CSR (and G^T) to the device, trim_run trims, trim_level copies the levels
-    back; all inside the host wall-clock timing."""
+def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None, mapped=True):
+    """Through the C ABI with host buffers, host wall clock around the whole
+    call sequence: trim_create on page-locked host CSR (and G^T), trim_run,
+    trim_level into a host array, trim_destroy. mapped: the kernels read the
+    host CSR in place over the CPU-GPU link (TRIM_MEM_HOST_MAPPED); otherwise
+    trim_create first copies it to device memory (TRIM_MEM_HOST)."""
     import torch
     pin = lambda a: torch.from_numpy(a.view(np.int32)).pin_memory()
     ho, ht, hoi, hti = pin(g.off), pin(g.tgt), pin(off_in), pin(tgt_in)
@@ -326,7 +337,7 @@ def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None):
     for s in range(steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with P.Trimmer(ho, ht, hoi, hti) as t:
+        with P.Trimmer(ho, ht, hoi, hti, host_mapped=mapped) as t:
             t.batch_run(graph_off, variant) if graph_off is not None else t.run(variant)
             P.trim_level(t.ctx, out.data_ptr(), 0)
         t1 = time.perf_counter()
@@ -351,7 +362,9 @@ def run_ours(args, rank, ws, local):
     have_model = os.path.exists(model)
     if have_model:
         t.set_model(np.load(model))
-    headline = args.variant or ("learned" if have_model else "heuristic")
+    # the plain variants are the measured schedules of the single-graph
+    # workloads; the large mixed graph runs the learned scheduler
+    headline = args.variant or ("learned" if (args.config == 4 and have_model) else "ac4")
     batched = g.graph_off is not None
     gofs = g.graph_off if batched else None
 
@@ -389,8 +402,14 @@ def run_ours(args, rank, ws, local):
     e2e = None
     if rank == 0 and args.e2e_steps > 0:
         ev, h2d, d2h = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs)
+        evc, _, _ = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs, False)
         e2e = {"value": ev * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h,
+               "inputs": "page-locked host CSR + G^T read in place by the kernels "
+                         "(TRIM_MEM_HOST_MAPPED, NVLink-C2C); levels copied back to host",
+               "copy_inputs_value": evc * ws,
+               "copy_inputs": "same calls with the CSR first copied to device memory "
+                              "(TRIM_MEM_HOST)"}
     t.close()
     if rank != 0:
         return
@@ -408,7 +427,7 @@ def run_ours(args, rank, ws, local):
                    "timing": "CUDA events on the library stream around reset + persistent kernel"},
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": st["launches"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(),
                      "kernel": "trim_persistent_kernel", "kernel_ms": kernel_ms,
@@ -417,6 +436,13 @@ def run_ours(args, rank, ws, local):
     }
     if sweep:
         line["variants"] = sweep
+        fixed = {v: sweep[v]["ms"] for v in ("ac4", "ac6", "ac3") if v in sweep}
+        if fixed:
+            best = min(fixed, key=fixed.get)
+            line["schedules"] = {"best_fixed": best, "best_fixed_ms": fixed[best]}
+            for v in ("heuristic", "learned"):
+                if v in sweep:
+                    line["schedules"][f"{v}_vs_best_fixed"] = fixed[best] / sweep[v]["ms"]
     if batched:
         line["config"]["graphs"] = int(len(g.graph_off) - 1)
         line["config"]["timing"] = ("CUDA events around trim_batch_run: one replayed CUDA graph "
@@ -440,7 +466,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--variant", default=None)
-    ap.add_argument("--sweep", action="store_true", help="also time every variant (stderr + JSON)")
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false",
+                    help="skip timing every variant next to the headline schedule")
     ap.add_argument("--sweep-variants", default="", help="comma-separated subset for --sweep")
     ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=5)

@@ -77,8 +77,21 @@ typedef struct {
   uint64_t m;
   const uint32_t* offsets;
   const uint32_t* targets;
-  int on_device; /* 1: device pointers (borrowed); 0: host pointers (copied) */
+  int on_device; /* where the arrays live: one of TRIM_MEM_* below                */
 } trim_csr_t;
+
+/* trim_csr_t.on_device */
+#define TRIM_MEM_HOST 0        /* host memory; trim_create copies it to the device          */
+#define TRIM_MEM_DEVICE 1      /* device memory of the context's GPU; borrowed, not copied  */
+#define TRIM_MEM_HOST_MAPPED 2 /* host memory the kernels read in place (borrowed, never
+                                  copied): page-locked memory (cudaHostAlloc,
+                                  cudaHostRegister), or any host memory on a system whose
+                                  GPU reads pageable memory through the host page tables
+                                  (coherent CPU-GPU links such as NVLink-C2C). The kernels
+                                  then fetch only the CSR entries they use, over the link;
+                                  trim_create fails with TRIM_ERR_INVALID_ARG if the GPU
+                                  cannot read the memory. The arrays must stay valid and
+                                  unchanged until trim_destroy. */
 
 /* flags of trim_create */
 #define TRIM_FLAG_VALIDATE 0x1u  /* check the CSR (and that csr_in is its transpose) on device */

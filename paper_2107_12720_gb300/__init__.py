@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 from .abi import (LIB_PATH, TRIM_AC3_PULL, TRIM_AC4_PUSH, TRIM_AC6_SUPPORT, TRIM_FLAG_ROUND_LOG,
-                  TRIM_FLAG_STATS, TRIM_FLAG_VALIDATE, TRIM_LIVE, TRIM_MLP_NBLOB,
+                  TRIM_FLAG_STATS, TRIM_FLAG_VALIDATE, TRIM_LIVE, TRIM_MEM_DEVICE, TRIM_MEM_HOST,
+                  TRIM_MEM_HOST_MAPPED, TRIM_MLP_NBLOB,
                   TRIM_MLP_NPARAMS, TRIM_SCHED_HEURISTIC, TRIM_SCHED_LEARNED,
                   TRIM_SCHED_SCRIPTED, TrimCsr, TrimError, TrimParams, TrimRoundRec,
                   TrimRunStats, lib, check)
@@ -53,12 +54,17 @@ class Trimmer:
 
     ``off``/``tgt`` (and optionally ``off_in``/``tgt_in`` for G^T) are uint32
     arrays: CUDA torch tensors are borrowed (kept alive by this object), numpy
-    arrays or CPU tensors are copied to the device by the library.
+    arrays or CPU tensors are copied to the device by the library, or, with
+    ``host_mapped=True``, read in place by the kernels (TRIM_MEM_HOST_MAPPED:
+    page-locked memory such as ``tensor.pin_memory()``, or any host memory on a
+    GPU that reads pageable memory; kept alive by this object).
     """
 
-    def __init__(self, off, tgt, off_in=None, tgt_in=None, stream=None, flags: int = 0):
+    def __init__(self, off, tgt, off_in=None, tgt_in=None, stream=None, flags: int = 0,
+                 host_mapped: bool = False):
         import torch
         self._keep = []
+        self._host_mode = TRIM_MEM_HOST_MAPPED if host_mapped else TRIM_MEM_HOST
         out_csr = self._csr(off, tgt)
         in_csr = self._csr(off_in, tgt_in) if off_in is not None else None
         if stream is None:
@@ -80,14 +86,15 @@ class Trimmer:
                 raise TrimError(1, "CSR tensors must be 32-bit integers")
             self._keep += [off, tgt]
             return TrimCsr(off.numel() - 1, tgt.numel(), off.data_ptr(),
-                           tgt.data_ptr() if tgt.numel() else None, 1)
+                           tgt.data_ptr() if tgt.numel() else None, TRIM_MEM_DEVICE)
         if isinstance(off, torch.Tensor):
+            self._keep += [off, tgt]  # a pinned tensor must outlive a mapped context
             off = off.numpy()
             tgt = tgt.numpy()
         off, tgt = _as_u32(off), _as_u32(tgt)
         self._keep += [off, tgt]
         return TrimCsr(off.shape[0] - 1, tgt.shape[0], off.ctypes.data,
-                       tgt.ctypes.data if tgt.size else None, 0)
+                       tgt.ctypes.data if tgt.size else None, self._host_mode)
 
     def run(self, variant="ac4") -> dict:
         return _stats_dict(trim_run(self.ctx, _variant(variant)))

@@ -17,6 +17,7 @@ TRIM_LIVE = 0xFFFFFFFF
 TRIM_AC4_PUSH, TRIM_AC6_SUPPORT, TRIM_AC3_PULL = 0, 1, 2
 TRIM_SCHED_HEURISTIC, TRIM_SCHED_LEARNED, TRIM_SCHED_SCRIPTED = 3, 4, 5
 TRIM_FLAG_VALIDATE, TRIM_FLAG_STATS, TRIM_FLAG_ROUND_LOG = 1, 2, 4
+TRIM_MEM_HOST, TRIM_MEM_DEVICE, TRIM_MEM_HOST_MAPPED = 0, 1, 2
 TRIM_MLP_NIN, TRIM_MLP_NH, TRIM_MLP_NOUT = 12, 32, 3
 TRIM_MLP_NPARAMS = 1571
 TRIM_MLP_NBLOB = TRIM_MLP_NPARAMS + 4 * TRIM_MLP_NIN

@@ -354,8 +354,36 @@ trim_err_t validate(trim_ctx* c, const uint32_t* ioff_given) {
   return TRIM_OK;
 }
 
+// Device-side address of host memory the kernels read in place
+// (TRIM_MEM_HOST_MAPPED): page-locked memory maps through its device pointer;
+// other host memory only where the GPU walks the host page tables.
+trim_err_t map_host(trim_ctx* c, const uint32_t* p, const uint32_t** out) {
+  *out = nullptr;
+  if (p == nullptr) return TRIM_OK;
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) (void)cudaGetLastError();
+  if (e == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) {
+    *out = static_cast<const uint32_t*>(at.devicePointer);
+    return TRIM_OK;
+  }
+  if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged))
+    return fail(c, TRIM_ERR_INVALID_ARG, "TRIM_MEM_HOST_MAPPED given device memory");
+  int pageable = 0;
+  CK(cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccessUsesHostPageTables,
+                            c->device));
+  if (!pageable)
+    return fail(c, TRIM_ERR_INVALID_ARG,
+                "host memory is not readable by this GPU: page-lock it or use TRIM_MEM_HOST");
+  *out = p;
+  return TRIM_OK;
+}
+
 trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, uint32_t flags,
                        trim_ctx* c) {
+  if (g->on_device < TRIM_MEM_HOST || g->on_device > TRIM_MEM_HOST_MAPPED ||
+      (gi && (gi->on_device < TRIM_MEM_HOST || gi->on_device > TRIM_MEM_HOST_MAPPED)))
+    return fail(c, TRIM_ERR_INVALID_ARG, "on_device must be one of TRIM_MEM_*");
   if (g->n > 0xFFFFFFFEu || g->m >= (1ull << 32))
     return fail(c, TRIM_ERR_TOO_LARGE, "n must be < 2^32-1 and m < 2^32");
   if (g->offsets == nullptr || (g->m && g->targets == nullptr))
@@ -366,12 +394,19 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
     if (gi->offsets == nullptr || (gi->m && gi->targets == nullptr))
       return fail(c, TRIM_ERR_INVALID_ARG, "csr_in: null array");
   }
-  if (!g->on_device && g->n) {
+  if (g->on_device == TRIM_MEM_HOST && g->n) {
     // cheap host checks before any device work
     if (g->offsets[0] != 0 || (uint64_t)g->offsets[g->n] != g->m)
       return fail(c, TRIM_ERR_BAD_GRAPH, "csr_out: offsets[0] != 0 or offsets[n] != m");
   }
   TRY(check_device(c, &c->device, &c->sm_count));
+  if (g->on_device == TRIM_MEM_HOST_MAPPED && g->n) {
+    // the same checks once the memory is known to be host memory
+    const uint32_t* probe = nullptr;
+    TRY(map_host(c, g->offsets, &probe));
+    if (g->offsets[0] != 0 || (uint64_t)g->offsets[g->n] != g->m)
+      return fail(c, TRIM_ERR_BAD_GRAPH, "csr_out: offsets[0] != 0 or offsets[n] != m");
+  }
   c->stream = static_cast<cudaStream_t>(stream);
   c->flags = flags;
   c->n = g->n;
@@ -383,9 +418,10 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
   const size_t n = c->n;
   if (flags & TRIM_FLAG_ROUND_LOG) c->rlog_cap = (uint32_t)std::min<uint64_t>(n + 1, 1u << 20);
   ArenaPlan A;
-  const size_t a_off = g->on_device ? 0 : A.add<uint32_t>(n + 1);
-  const size_t a_tgt = g->on_device ? 0 : A.add<uint32_t>(c->m);
-  const bool in_host = gi && !gi->on_device;
+  const bool out_host = g->on_device == TRIM_MEM_HOST;
+  const size_t a_off = out_host ? A.add<uint32_t>(n + 1) : 0;
+  const size_t a_tgt = out_host ? A.add<uint32_t>(c->m) : 0;
+  const bool in_host = gi && gi->on_device == TRIM_MEM_HOST;
   const size_t a_ioff = in_host ? A.add<uint32_t>(n + 1) : 0;
   const size_t a_itgt = in_host ? A.add<uint32_t>(c->m) : 0;
   const size_t a_level = A.add<uint32_t>(n), a_cnt = A.add<uint32_t>(n), a_supp = A.add<uint32_t>(n);
@@ -401,12 +437,15 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
   char* base = nullptr;
   TRY(dalloc(c, &base, A.bytes));
   auto at = [&](size_t o) { return reinterpret_cast<uint32_t*>(base + o); };
-  if (!g->on_device) {
+  if (out_host) {
     CK(cudaMemcpyAsync(at(a_off), g->offsets, (n + 1) * 4, cudaMemcpyHostToDevice, c->stream));
     if (c->m)
       CK(cudaMemcpyAsync(at(a_tgt), g->targets, c->m * 4, cudaMemcpyHostToDevice, c->stream));
     c->off = at(a_off);
     c->tgt = at(a_tgt);
+  } else if (g->on_device == TRIM_MEM_HOST_MAPPED) {
+    TRY(map_host(c, g->offsets, &c->off));
+    TRY(map_host(c, c->m ? g->targets : nullptr, &c->tgt));
   } else {
     c->off = g->offsets;
     c->tgt = g->targets;
@@ -418,6 +457,9 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
         CK(cudaMemcpyAsync(at(a_itgt), gi->targets, c->m * 4, cudaMemcpyHostToDevice, c->stream));
       c->ioff = at(a_ioff);
       c->itgt = at(a_itgt);
+    } else if (gi->on_device == TRIM_MEM_HOST_MAPPED) {
+      TRY(map_host(c, gi->offsets, &c->ioff));
+      TRY(map_host(c, c->m ? gi->targets : nullptr, &c->itgt));
     } else {
       c->ioff = gi->offsets;
       c->itgt = gi->targets;

@@ -65,6 +65,9 @@ def test_host_argument_checks_without_device(lib):
     bad = TrimCsr(2, 3, off.ctypes.data, tgt.ctypes.data, 0)
     assert lib.trim_create(ctypes.byref(bad), None, None, 0, ctypes.byref(ctx)) == 2
     assert "offsets" in lib.trim_last_error(None).decode()
+    # unknown memory kind
+    odd = TrimCsr(2, 2, off.ctypes.data, tgt.ctypes.data, 7)
+    assert lib.trim_create(ctypes.byref(odd), None, None, 0, ctypes.byref(ctx)) == 1
     # csr_in of a different size
     cin = TrimCsr(3, 2, off.ctypes.data, tgt.ctypes.data, 0)
     assert lib.trim_create(ctypes.byref(csr), ctypes.byref(cin), None, 0, ctypes.byref(ctx)) == 1
@@ -95,3 +98,14 @@ def test_mlp_entry_points_reject_bad_args(lib):
     assert lib.trim_mlp_loss_grad(None, None, None, 0, None, None, None, None) == 1
     assert lib.trim_mlp_adam_step(None, None, None, None, 0, 0.0, 0.0, 0.0, 0.0, None) == 1
     assert lib.trim_mlp_scratch_bytes(1000) > 0
+
+
+def test_header_constants_match_binding():
+    """#define values of include/trim.h that the binding mirrors."""
+    import re
+    from paper_2107_12720_gb300 import abi
+    hdr = open(os.path.join(ROOT, "include", "trim.h")).read()
+    defs = dict(re.findall(r"#define (TRIM_[A-Z0-9_]+) \(?([0-9xA-Fa-f]+)u?", hdr))
+    for name in ["TRIM_MEM_HOST", "TRIM_MEM_DEVICE", "TRIM_MEM_HOST_MAPPED", "TRIM_FLAG_VALIDATE",
+                 "TRIM_FLAG_STATS", "TRIM_FLAG_ROUND_LOG"]:
+        assert int(defs[name], 0) == getattr(abi, name), name

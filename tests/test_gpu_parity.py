@@ -118,6 +118,50 @@ def test_host_inputs_and_device_transpose(i):
             check(t, lvl, st, alpha, v, t.run(v))
 
 
+@pytest.mark.parametrize("i", [0, 1, 2, 3])
+def test_host_mapped_inputs(i):
+    """TRIM_MEM_HOST_MAPPED: the kernels read page-locked host CSR arrays (G and
+    G^T) in place; every variant must match the oracle, and so must a graph
+    given without G^T (AC-4 then builds G^T on the device from the host CSR)."""
+    import torch
+    P = _P()
+    g = cfg.config_small(i)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    oi, ti = oracle.transpose(g.off, g.tgt)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
+    with P.Trimmer(pin(g.off), pin(g.tgt), pin(oi), pin(ti), host_mapped=True) as t:
+        for v in VARIANTS:
+            check(t, lvl, st, alpha, "mapped-" + v, t.run(v))
+        if g.graph_off is not None:
+            s = t.batch_run(np.asarray(g.graph_off, np.uint32), "ac4")
+            check(t, lvl, st, alpha, "mapped-batch", s)
+    with P.Trimmer(pin(g.off), pin(g.tgt), host_mapped=True) as t:
+        for v in ["ac6", "ac4"]:
+            check(t, lvl, st, alpha, "mapped-noGT-" + v, t.run(v))
+
+
+def test_host_mapped_pageable_or_refused():
+    """Pageable (plain numpy) memory with TRIM_MEM_HOST_MAPPED is read in place
+    on GPUs that walk the host page tables, and refused with
+    TRIM_ERR_INVALID_ARG elsewhere; device memory is always refused."""
+    import torch
+    P = _P()
+    g = cfg.config_small(1)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    try:
+        t = P.Trimmer(g.off.copy(), g.tgt.copy(), host_mapped=True)
+    except P.TrimError as e:
+        assert e.code == 1 and "page-lock" in str(e)
+    else:
+        with t:
+            check(t, lvl, st, alpha, "pageable-ac6", t.run("ac6"))
+    off, tgt = dev_csr(g)
+    csr = P.abi.TrimCsr(g.n, g.m, off.data_ptr(), tgt.data_ptr(), P.TRIM_MEM_HOST_MAPPED)
+    with pytest.raises(P.TrimError) as e:
+        P.trim_create(csr, None, None, 0)
+    assert e.value.code == 1
+
+
 def test_random_schedules_are_bit_identical():
     """Property: any per-round mix of the three kernels gives the same levels."""
     P = _P()
