@@ -102,9 +102,13 @@ typedef struct {
 typedef struct {
   uint32_t block_threads;     /* threads per CTA of the persistent kernel (128..512, x32)  */
   uint32_t ctas_per_sm;       /* persistent CTAs per SM (0 = as many as fit)               */
-  uint32_t batch_cta_max_n;   /* batched: graphs with at most this many vertices run in
-                                 one CTA (0 = never)                                         */
-  uint32_t batch_cta_max_m;   /* batched: ... and at most this many edges                   */
+  uint32_t sched_commit_rounds; /* HEURISTIC / LEARNED trim_run: after this many rounds
+                                 in a row with the same choice, the run commits to that
+                                 variant and continues on its single-variant kernel, with
+                                 no feature or scheduling work (0 = never commit)        */
+  uint32_t sched_recheck_rounds; /* ... a committed stretch lasts this many rounds, then the
+                                 scheduler is consulted again; each stretch that ends in
+                                 the same commit doubles the next one                    */
   uint64_t spin_limit_ns;     /* bound of every device-side wait; past it the run stops
                                  with TRIM_ERR_TIMEOUT                                       */
   float heur_push_ratio;      /* heuristic: push while sum(indeg F) < ratio * n_live        */
@@ -195,10 +199,11 @@ trim_err_t trim_level_device_ptr(const trim_ctx* ctx, const uint32_t** out);
 /* Batched trimming of G independent graphs packed into the context's CSR:
  * graph g owns vertices [graph_off[g], graph_off[g+1]) and no edge may cross two
  * graphs (checked with TRIM_FLAG_VALIDATE). graph_off: G+1 host uint32 values,
- * graph_off[0]=0, graph_off[G]=n. Graphs small enough (trim_params_t
- * batch_cta_max_n / _m) are trimmed whole inside one CTA each; the rest join a
- * grid-wide round loop run with `variant`. Results equal trimming each graph
- * alone (and the union at once): read them with trim_status / trim_level. */
+ * graph_off[0]=0, graph_off[G]=n. The packed CSR is the disjoint union of the
+ * graphs, so all of them are trimmed by one persistent launch of `variant`
+ * (captured into a CUDA graph and replayed from the second call with the same
+ * variant on): every round serves every graph still peeling. Results equal
+ * trimming each graph alone: read them with trim_status / trim_level. */
 trim_err_t trim_batch_run(trim_ctx* ctx, const uint32_t* graph_off, uint32_t G,
                           trim_variant_t variant, trim_run_stats_t* stats);
 

@@ -39,7 +39,7 @@ class TrimCsr(ctypes.Structure):
 
 class TrimParams(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("batch_cta_max_n", ctypes.c_uint32), ("batch_cta_max_m", ctypes.c_uint32),
+                ("sched_commit_rounds", ctypes.c_uint32), ("sched_recheck_rounds", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("heur_push_ratio", ctypes.c_float),
                 ("heur_ac6_ratio", ctypes.c_float)]
 

@@ -191,8 +191,8 @@ trim_err_t check_device(trim_ctx* c, int* dev, int* sms) {
 void default_params(trim_params_t* p) {
   p->block_threads = 512;
   p->ctas_per_sm = 0;
-  p->batch_cta_max_n = 4096;
-  p->batch_cta_max_m = 65536;
+  p->sched_commit_rounds = 8;
+  p->sched_recheck_rounds = 64;
   p->spin_limit_ns = 5ull * 1000 * 1000 * 1000;  // 5 s
   p->heur_push_ratio = 1.0f;
   p->heur_ac6_ratio = 1.0f;
@@ -493,7 +493,8 @@ trim_err_t ensure_work_list(trim_ctx* c) {
 
 // Enqueues one run. A scheduled variant runs on the all-variant kernel, or with
 // seg_flavour >= 0 as the first segment of a segmented run (run_segmented).
-trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1) {
+trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1,
+                       uint32_t commit_after = 0) {
   if ((int)variant < 0 || variant > TRIM_SCHED_SCRIPTED)
     return fail(c, TRIM_ERR_INVALID_ARG, "unknown variant");
   if (variant == TRIM_SCHED_SCRIPTED && c->script_len == 0)
@@ -555,6 +556,10 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   D.spin_limit_ns = c->params.spin_limit_ns;
   D.heur_push_ratio = c->params.heur_push_ratio;
   D.heur_ac6_ratio = c->params.heur_ac6_ratio;
+  D.commit_after = commit_after;
+  D.stop_round = 0;
+  // segmented scheduled runs keep the live-edge count through lean stretches
+  if (variant >= TRIM_SCHED_HEURISTIC && seg_flavour >= 0) D.flags |= trimk::F_LIVE_EDGES;
   // a fixed variant runs on its lean single-variant flavour
   int flavour = kFlavourAll;
   if (variant <= TRIM_AC3_PULL) flavour = (int)variant;
@@ -580,12 +585,16 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   return TRIM_OK;
 }
 
-// Launches the next segment of a segmented run: the flavour of the variant the
-// scheduler picked, resuming from the schedule state the last segment saved.
-trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base) {
+// Launches the next segment of a segmented run, resuming from the schedule
+// state the last segment saved: `flavour` runs with `mode` (the scheduled mode,
+// or a fixed variant for a committed stretch that hands back at stop_round).
+trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base, uint32_t mode,
+                          uint32_t stop_round) {
   trimk::Dev D = c->last_dev;
   D.resume = 1;
   D.bar_base = bar_base;
+  D.mode = mode;
+  D.stop_round = stop_round;
   c->last_flavour = flavour;
   void* args[] = {&D};
   CK(cudaLaunchCooperativeKernel((const void*)kFlavours[flavour], dim3(c->grids[flavour]),
@@ -598,20 +607,30 @@ trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base) {
 trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read = false);
 
 // A scheduled run (heuristic, learned, scripted) on the lean kernels: each
-// segment is one cooperative launch of the flavour that holds one variant plus
-// the schedulers. When the scheduler picks a variant the running kernel lacks,
-// the kernel saves the schedule state and exits; the host reads the handover
-// and launches the flavour of that variant, which resumes at the same round.
-// The first segment starts on the flavour this mode's last run started with.
+// segment is one cooperative launch. The scheduler runs on the flavour that
+// holds one variant plus the schedulers; when it picks a variant the running
+// kernel lacks, the kernel saves the schedule state and exits, and the host
+// launches the flavour of that variant, which resumes at the same round. When
+// the heuristic or learned scheduler has kept its choice for
+// sched_commit_rounds rounds, the run commits: the next segment is the
+// single-variant kernel of that variant (no features, no scheduling) for
+// sched_recheck_rounds rounds, after which the scheduler is consulted again;
+// a stretch that ends in the same commit doubles the next one. The first
+// segment starts on the flavour this mode's last run started with.
 trim_err_t run_segmented(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats) {
   const int mi = (int)variant - (int)TRIM_SCHED_HEURISTIC;
   int first = c->seg_first[mi];
   if (first < 0 && variant == TRIM_SCHED_SCRIPTED && !c->h_script.empty())
     first = kFlavourSeg + std::min<int>(c->h_script[0], TRIM_AC3_PULL);
   if (first < 0) first = kFlavourSeg + (c->ioff ? TRIM_AC4_PUSH : TRIM_AC3_PULL);
-  TRY(enqueue_run(c, variant, first));
+  const uint32_t commit_after =
+      variant == TRIM_SCHED_SCRIPTED ? 0u : c->params.sched_commit_rounds;
+  TRY(enqueue_run(c, variant, first, commit_after));
   if (!c->pending) return finish_run(c, stats);
   uint64_t segments = 1;
+  uint64_t period = std::max<uint32_t>(1u, c->params.sched_recheck_rounds);
+  int last_commit = -1;
+  bool lean = false;  // the last segment was a committed single-variant stretch
   while (true) {
     TRY(sync_check(c));
     CK(cudaMemcpy(c->h_ctrl, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
@@ -622,9 +641,21 @@ trim_err_t run_segmented(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* 
       c->s_cnt_dirty = true;
       return fail(c, TRIM_ERR_STATE, "invalid segment handover");
     }
-    const int next = kFlavourSeg + (int)h.resume_variant;
-    if (h.saved.round == 1) c->seg_first[mi] = next;
-    TRY(launch_segment(c, next, h.bar));
+    const uint32_t v = h.resume_variant, round = h.saved.round;
+    if (h.commit) {
+      period = ((int)v == last_commit) ? std::min<uint64_t>(period * 2, 1u << 30)
+                                       : std::max<uint32_t>(1u, c->params.sched_recheck_rounds);
+      last_commit = (int)v;
+      const uint64_t stop = std::min<uint64_t>((uint64_t)round + period, 0xFFFFFFFFull);
+      TRY(launch_segment(c, (int)v, h.bar, v, (uint32_t)stop));
+      lean = true;
+    } else {
+      // a committed stretch reached its end, or the scheduler picked a
+      // variant the running kernel lacks: the scheduler flavour of v resumes
+      if (!lean && round == 1) c->seg_first[mi] = kFlavourSeg + (int)v;
+      TRY(launch_segment(c, kFlavourSeg + (int)v, h.bar, (uint32_t)variant, 0u));
+      lean = false;
+    }
   }
   c->last_segments = segments;
   return finish_run(c, stats, true);
@@ -864,6 +895,8 @@ trim_err_t trim_set_params(trim_ctx* c, const trim_params_t* p) {
   if (p->spin_limit_ns == 0) return fail(c, TRIM_ERR_INVALID_ARG, "spin_limit_ns must be > 0");
   if (!(p->heur_push_ratio > 0.0f) || !(p->heur_ac6_ratio > 0.0f))
     return fail(c, TRIM_ERR_INVALID_ARG, "heuristic ratios must be > 0");
+  if (p->sched_commit_rounds && !p->sched_recheck_rounds)
+    return fail(c, TRIM_ERR_INVALID_ARG, "sched_recheck_rounds must be > 0 when committing");
   drop_batch_graph(c);
   const trim_params_t old = c->params;
   c->params = *p;

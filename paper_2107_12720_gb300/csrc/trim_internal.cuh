@@ -26,6 +26,7 @@ constexpr uint32_t F_NEED_FEATURES = 0x100;  // scheduler modes: gather per-fron
 constexpr uint32_t F_AC4_POSSIBLE = 0x200;   // counters initialised, AC-4 work list kept
 constexpr uint32_t F_AC6_POSSIBLE = 0x400;
 constexpr uint32_t F_AC3_POSSIBLE = 0x800;
+constexpr uint32_t F_LIVE_EDGES = 0x1000;    // scheduled run: keep the live-edge count in every flavour
 
 // Per-round accumulators, filled while round r runs (ring slot r & 3). CTA 0
 // zeroes slot (k+2) & 3 at the start of round k: that slot was last read at the
@@ -57,6 +58,7 @@ struct Sched {
   uint32_t fprev;         // frontier size of round r-1 (timing feature)
   uint32_t mixed;         // 1 once a round ran AC-6 or AC-3 (AC-4 must then re-check levels)
   uint32_t vcount[3];     // rounds run so far by AC-4, AC-6, AC-3
+  uint32_t stable;        // rounds in a row the scheduler kept its choice (0 outside schedulers)
   unsigned long long m_live;     // out-edges of live vertices
   float feat[12];                // features that chose this round's variant
 };
@@ -82,7 +84,7 @@ struct Ctrl {
   unsigned int resume;            // 1: a segment ended early, state in `saved`
   unsigned int resume_variant;    // the variant the next segment must run
   unsigned int segments;          // kernels run so far in this run
-  unsigned int _p5;
+  unsigned int commit;            // 1: the segment ended because the scheduler committed
   Sched saved;
 };
 
@@ -113,6 +115,8 @@ struct Dev {
   uint32_t* bsum;     // per-CTA scratch of the grid-wide scan
   uint32_t sbuf_cap;  // entries of each CTA append buffer (dynamic shared memory)
   uint32_t resume;    // 1: continue the run from Ctrl::saved instead of starting it
+  uint32_t stop_round;    // != 0: hand the run back to the host at the start of this round
+  uint32_t commit_after;  // != 0: scheduler flavours commit after this many stable rounds
   uint32_t bar_base;  // grid-barrier counter when this kernel starts (0 for a new run)
   Ctrl* C;
   trim_round_rec_t* rlog;

@@ -214,9 +214,9 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   const unsigned mask = __ballot_sync(FULL, pred);
   if (mask == 0u) return;
   const bool feats = (MODES & M_SCHED) && (D.flags & F_NEED_FEATURES);
-  // every flavour that may hand the run to AC-4 keeps its work list complete
-  constexpr bool may4 = (MODES & (M_AC4 | M_SCHED)) != 0;
-  const bool track = D.ioff != nullptr && ((may4 && (D.flags & F_AC4_POSSIBLE)) || feats);
+  const bool live_edges = feats || (D.flags & F_LIVE_EDGES);
+  // whenever the run may use AC-4, every flavour keeps its work list complete
+  const bool track = D.ioff != nullptr && ((D.flags & F_AC4_POSSIBLE) || feats);
   uint32_t row = 0, din = 0;
   if (!pred) dout = 0;
   if (pred && track) {
@@ -228,7 +228,7 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
       din = __ldg(&D.ioff[u + 1]) - row;
     }
   }
-  const bool w = may4 && pred && din > 0u && (D.flags & F_AC4_POSSIBLE);
+  const bool w = pred && din > 0u && (D.flags & F_AC4_POSSIBLE);
   const unsigned wmask = __ballot_sync(FULL, w);
   const unsigned lt = (1u << lane) - 1u;
   const unsigned k = __popc(mask), kw = __popc(wmask);
@@ -250,8 +250,8 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   }
   unsigned s_in = 0, s_out = 0;
   unsigned h0 = 0, h1 = 0;
+  if (live_edges) s_out = __reduce_add_sync(FULL, dout);
   if (feats) {
-    s_out = __reduce_add_sync(FULL, dout);
     s_in = __reduce_add_sync(FULL, din);
     h0 = __popc(__ballot_sync(FULL, pred && din < 8u));
     h1 = __popc(__ballot_sync(FULL, pred && din >= 8u && din < 256u));
@@ -262,9 +262,9 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
     ws.ncount += k - kl;
     ws.nw4 = pw + kw;
     ws.nedge = pe + esum;
+    if (live_edges) ws.sum_out += s_out;
     if (feats) {
       ws.sum_in += s_in;
-      ws.sum_out += s_out;
       ws.hist[0] += h0;
       ws.hist[1] += h1;
       ws.hist[2] += k - h0 - h1;
@@ -323,14 +323,16 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
       if (lane == 0) set_error(D, TRIM_ERR_STATE, 0xD6);
       vb = 0xFFFFFFFFu;
     }
+    if (((MODES & M_SCHED) && (D.flags & F_NEED_FEATURES)) || (D.flags & F_LIVE_EDGES)) {
+      const uint32_t s_out = __reduce_add_sync(FULL, has ? B.ws[lane].sum_out : 0u);
+      if (lane == 4 && s_out) atomicAdd(&rs->sum_out, (unsigned long long)s_out);
+    }
     if ((MODES & M_SCHED) && (D.flags & F_NEED_FEATURES)) {
       const uint32_t s_in = __reduce_add_sync(FULL, has ? B.ws[lane].sum_in : 0u);
-      const uint32_t s_out = __reduce_add_sync(FULL, has ? B.ws[lane].sum_out : 0u);
       uint32_t h[3];
       for (int i = 0; i < 3; ++i) h[i] = __reduce_add_sync(FULL, has ? B.ws[lane].hist[i] : 0u);
-      // five lanes, five independent reductions (no return value: no wait)
+      // independent reductions from separate lanes (no return value: no wait)
       if (lane == 3 && s_in) atomicAdd(&rs->sum_in, (unsigned long long)s_in);
-      if (lane == 4 && s_out) atomicAdd(&rs->sum_out, (unsigned long long)s_out);
       if (lane >= 5 && lane < 8 && h[lane - 5]) atomicAdd(&rs->hist[lane - 5], h[lane - 5]);
     }
     if (has) {
@@ -558,9 +560,10 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
   const uint32_t live_count = ld_relaxed(&rs->live_count);
   unsigned long long sum_in = 0, sum_out = 0, t_r = 0, t_rm1 = 0;
   uint32_t h0 = 0, h1 = 0, h2 = 0;
+  const bool live_edges = feats || (D.flags & F_LIVE_EDGES);
+  if (live_edges) sum_out = ld_relaxed64(&rs->sum_out);
   if (feats) {
     sum_in = ld_relaxed64(&rs->sum_in);
-    sum_out = ld_relaxed64(&rs->sum_out);
     h0 = ld_relaxed(&rs->hist[0]);
     h1 = ld_relaxed(&rs->hist[1]);
     h2 = ld_relaxed(&rs->hist[2]);
@@ -602,6 +605,15 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
     D.roff[r + 1] = len;
     C->rounds = nF ? r + 1 : r;
   }
+  // live-edge count. With G^T and a complete AC-4 work list: edges between live
+  // vertices = m minus the in-edges of removed vertices (a removed vertex has
+  // only removed successors, so every edge that touches one ends in one).
+  // Otherwise: with G^T, the same from the in-degree sums; without it, out-edges
+  // of live vertices (AC-3/AC-6 know each removed vertex's degree).
+  if (live_edges) {
+    if (D.ioff != nullptr && (D.flags & F_AC4_POSSIBLE)) L.m_live = (unsigned long long)D.m - e_end;
+    else L.m_live -= (D.ioff != nullptr) ? sum_in : sum_out;
+  }
   if (nF == 0) {
     L.done = 1;
   } else {
@@ -609,11 +621,6 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
     float f[NFEAT];
     for (int i = 0; i < NFEAT; ++i) f[i] = 0.0f;
     if (feats) {
-      // live-edge count. With G^T: edges between live vertices, i.e. m minus the
-      // in-edges of removed vertices (a removed vertex has only removed
-      // successors, so every edge that touches one ends in one). Without G^T:
-      // out-edges of live vertices (AC-3/AC-6 know each removed vertex's degree).
-      L.m_live -= (D.ioff != nullptr) ? sum_in : sum_out;
       f[0] = log2p1((float)nF);
       f[1] = log2p1((float)sum_in);
       f[2] = log2p1((float)(e_end - L.e_c4));  // in-edges AC-4 has not pushed yet
@@ -647,6 +654,9 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
         if (in_range) next = learned;
       }
     }
+    // rounds in a row with an unchanged choice (a flavour without the
+    // schedulers makes no choice: a resumed scheduler starts counting afresh)
+    L.stable = !(MODES & M_SCHED) ? 0u : (r >= 1 && next == L.variant) ? L.stable + 1u : 1u;
     L.prev_variant = (r >= 1) ? L.variant : NIL;
     L.fprev = L.fe - L.fb;  // frontier of round r, for the timing feature two rounds on
     L.variant = next;
@@ -1033,6 +1043,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     S.ac3_list = NIL; S.live_in_len = 0; S.live_out = 0;
     S.done = 0; S.fprev = 0; S.mixed = 0;
     S.vcount[0] = S.vcount[1] = S.vcount[2] = 0;
+    S.stable = 0;
     S.m_live = D.m;
     for (int i = 0; i < NFEAT; ++i) S.feat[i] = 0.0f;
 
@@ -1090,14 +1101,19 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     const bool have = (S.variant == TRIM_AC4_PUSH && (MODES & M_AC4)) ||
                       (S.variant == TRIM_AC6_SUPPORT && (MODES & M_AC6)) ||
                       (S.variant == TRIM_AC3_PULL && (MODES & M_AC3));
-    if (!have) {
-      // this kernel lacks the chosen variant: hand the run to the kernel that
-      // has it (every CTA took the same decision, so all stop here)
+    // Hand the run to the host at the start of this round (every CTA takes the
+    // same decision from the same state, so all stop here): this kernel lacks
+    // the chosen variant; or the host asked to get the run back at this round;
+    // or the scheduler kept its choice long enough to commit to it.
+    const bool stop = D.stop_round != 0u && S.round >= D.stop_round;
+    const bool commit = (MODES & M_SCHED) && D.commit_after != 0u && S.stable >= D.commit_after;
+    if (!have || stop || commit) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         volatile uint32_t* w = reinterpret_cast<volatile uint32_t*>(&D.C->saved);
         const uint32_t* src = reinterpret_cast<const uint32_t*>(&B.S);
         for (unsigned i = 0; i < sizeof(Sched) / 4; ++i) w[i] = src[i];
         D.C->resume_variant = S.variant;
+        D.C->commit = (have && !stop && commit) ? 1u : 0u;
         __threadfence();
         D.C->resume = 1;
       }

@@ -213,14 +213,65 @@ def test_segmented_runs_match_single_launch():
                 assert s1["segments"] == 1
                 assert [r.variant for r in t.round_log()] == want_v
             for mode in ["heuristic", "learned"]:
+                # without commits the segmented run takes the single launch's choices
+                t.set_params(sched_commit_rounds=0)
                 s = t.run(mode)
                 check(t, lvl, st, alpha, mode, s)
                 seg_v = [r.variant for r in t.round_log()]
-                assert s["segments"] == 1 + sum(1 for a, b in zip(seg_v, seg_v[1:]) if a != b) \
-                    or s["segments"] == 2 + sum(1 for a, b in zip(seg_v, seg_v[1:]) if a != b)
+                changes = sum(1 for a, b in zip(seg_v, seg_v[1:]) if a != b)
+                assert s["segments"] in (1 + changes, 2 + changes)
                 t.run_async(mode)
                 check(t, lvl, st, alpha, mode + "-single", t.sync())
                 assert [r.variant for r in t.round_log()] == seg_v
+                # with commits: same result, rounds split over the kernels as logged
+                t.set_params(sched_commit_rounds=4, sched_recheck_rounds=16)
+                s = t.run(mode)
+                check(t, lvl, st, alpha, mode + "-commit", s)
+                log = t.round_log()
+                assert len(log) == alpha
+                assert list(np.bincount([r.variant for r in log], minlength=3)) == \
+                    list(s["rounds_by_variant"])
+                t.set_params(sched_commit_rounds=8, sched_recheck_rounds=64)
+
+
+def test_committed_stretches_on_a_deep_cascade():
+    """A deep cascade (hundreds of rounds) with the heuristic choosing AC-4 every
+    round: after sched_commit_rounds stable rounds the run moves to the AC-4-only
+    kernel for stretches of 16, 32, 64, ... rounds, consulting the scheduler
+    between them. The launch count follows from that rule exactly; the levels
+    equal the oracle's."""
+    P = _P()
+    g = cfg.config_small(2)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    off, tgt = dev_csr(g)
+    oi, ti = dev_csr_in(g)
+    K, P0 = 4, 16
+    with P.Trimmer(off, tgt, oi, ti, flags=P.TRIM_FLAG_ROUND_LOG) as t:
+        t.set_params(sched_commit_rounds=K, sched_recheck_rounds=P0)
+        s = t.run("heuristic")
+        check(t, lvl, st, alpha, "heuristic-commit", s)
+        assert s["rounds_by_variant"] == [alpha, 0, 0]
+        assert s["segments"] == _commit_segments(alpha, K, P0), (s["segments"], alpha)
+
+
+def _commit_segments(alpha, K, P0):
+    """Launches of a scheduled run whose choice never changes: rounds 1..alpha;
+    the choice has been kept for K rounds at the start of round K, where the run
+    commits; a stretch from round r runs to the start of round r+p (p = P0,
+    doubling); the scheduler then counts K rounds afresh before committing."""
+    segs, r, p = 1, K, P0
+    if r > alpha:
+        return segs
+    while True:
+        segs += 1                # committed stretch from round r
+        end = r + p
+        if end > alpha:          # the run ends inside the stretch
+            return segs
+        segs += 1                # scheduler kernel from round `end`
+        r = end + K
+        if r > alpha:
+            return segs
+        p *= 2
 
 
 def test_random_graphs_with_duplicates_and_loops():
