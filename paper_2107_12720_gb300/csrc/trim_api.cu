@@ -42,7 +42,8 @@ struct trim_ctx {
            *log = nullptr, *roff = nullptr, *live0 = nullptr, *live1 = nullptr, *bsum = nullptr;
   uint32_t *w4_row = nullptr, *w4_eoff = nullptr, *chunk_first = nullptr;
   Ctrl* ctrl = nullptr;
-  Ctrl* h_ctrl = nullptr;  // pinned host mirror for read-back
+  Ctrl* h_ctrl = nullptr;  // host mirror of the control block for read-back
+  bool h_ctrl_pinned = false;
   trim_round_rec_t* rlog = nullptr;
   uint32_t rlog_cap = 0;
   float* model = nullptr;
@@ -158,6 +159,40 @@ struct ArenaPlan {
     if (t_ != TRIM_OK) return t_;    \
   } while (0)
 
+// Page-locked host slots for the control-block mirrors: a read-back into
+// page-locked memory is a short DMA, into pageable memory a staged copy. The
+// slots come from one block allocated on first use and shared by all contexts
+// of the process (page-locking per context would cost more than it saves).
+constexpr int kCtrlSlots = 64;
+std::mutex g_slot_mutex;
+char* g_slot_block = nullptr;
+bool g_slot_used[kCtrlSlots] = {};
+constexpr size_t kSlotBytes = (sizeof(Ctrl) + 255) / 256 * 256;
+
+Ctrl* take_ctrl_slot() {
+  std::lock_guard<std::mutex> lock(g_slot_mutex);
+  if (!g_slot_block) {
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, kSlotBytes * kCtrlSlots, cudaHostAllocPortable) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    g_slot_block = static_cast<char*>(p);
+  }
+  for (int i = 0; i < kCtrlSlots; ++i)
+    if (!g_slot_used[i]) {
+      g_slot_used[i] = true;
+      return new (g_slot_block + i * kSlotBytes) Ctrl();
+    }
+  return nullptr;
+}
+
+void give_ctrl_slot(Ctrl* h) {
+  std::lock_guard<std::mutex> lock(g_slot_mutex);
+  const int i = (int)((reinterpret_cast<char*>(h) - g_slot_block) / (ptrdiff_t)kSlotBytes);
+  if (i >= 0 && i < kCtrlSlots) g_slot_used[i] = false;
+}
+
 void release(trim_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
@@ -165,7 +200,9 @@ void release(trim_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void* p : c->owned) cudaFreeAsync(p, c->stream);
   c->owned.clear();
-  delete c->h_ctrl;
+  if (c->h_ctrl_pinned) give_ctrl_slot(c->h_ctrl);
+  else delete c->h_ctrl;
+  c->h_ctrl = nullptr;
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
 }
@@ -191,8 +228,8 @@ trim_err_t check_device(trim_ctx* c, int* dev, int* sms) {
 void default_params(trim_params_t* p) {
   p->block_threads = 512;
   p->ctas_per_sm = 0;
-  p->sched_commit_rounds = 8;
-  p->sched_recheck_rounds = 64;
+  p->sched_commit_rounds = 32;
+  p->sched_recheck_rounds = 128;
   p->spin_limit_ns = 5ull * 1000 * 1000 * 1000;  // 5 s
   p->heur_push_ratio = 1.0f;
   p->heur_ac6_ratio = 1.0f;
@@ -260,6 +297,12 @@ trim_err_t sync_check(trim_ctx* c) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
   return TRIM_OK;
+}
+
+// Waits for the stream and copies the control block to the host mirror.
+trim_err_t read_ctrl(trim_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_ctrl, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  return sync_check(c);
 }
 
 // exclusive scan of in[0..n) into out[0..n], out[n] = total (device, on c->stream)
@@ -474,7 +517,9 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
   if (c->rlog_cap) c->rlog = reinterpret_cast<trim_round_rec_t*>(base + a_rlog);
   if (flags & TRIM_FLAG_VALIDATE) TRY(validate(c, gi ? c->ioff : nullptr));
   CK(cudaMemsetAsync(c->s_cnt, 0, n * 4, c->stream));
-  c->h_ctrl = new (std::nothrow) Ctrl();
+  c->h_ctrl = take_ctrl_slot();
+  c->h_ctrl_pinned = c->h_ctrl != nullptr;
+  if (!c->h_ctrl) c->h_ctrl = new (std::nothrow) Ctrl();
   if (!c->h_ctrl) return fail(c, TRIM_ERR_OOM, "host allocation failed");
   TRY(compute_grid(c));
   TRY(sync_check(c));
@@ -632,8 +677,7 @@ trim_err_t run_segmented(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* 
   int last_commit = -1;
   bool lean = false;  // the last segment was a committed single-variant stretch
   while (true) {
-    TRY(sync_check(c));
-    CK(cudaMemcpy(c->h_ctrl, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    TRY(read_ctrl(c));
     const Ctrl& h = *c->h_ctrl;
     if (h.err || !h.resume) break;
     if (h.resume_variant > TRIM_AC3_PULL || ++segments > (uint64_t)c->n + 3) {
@@ -665,10 +709,7 @@ trim_err_t run_segmented(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* 
 // control block is already in h_ctrl).
 trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read) {
   if (c->pending) {
-    if (!ctrl_read) {
-      TRY(sync_check(c));
-      CK(cudaMemcpy(c->h_ctrl, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
-    }
+    if (!ctrl_read) TRY(read_ctrl(c));
     c->pending = false;
     const Ctrl& h = *c->h_ctrl;
     if (h.err) {

@@ -162,13 +162,25 @@ def predict(theta, Xn):
     return out.cpu().numpy()
 
 
+# features that are log2 of a size (frontier, edges, live counts, time per
+# vertex): the model may extrapolate them to larger or smaller graphs, by up to
+# LOG2_MARGIN binary orders of magnitude outside the training range
+LOG2_FEATURES = (0, 1, 2, 3, 4, 10)
+LOG2_MARGIN = 8.0
+
+
 def make_blob(theta, mean, istd, X, margin=0.25):
-    """Model blob for trim_set_model: parameters, normalisation, and the training
-    range of every feature widened by `margin` of its span."""
+    """Model blob for trim_set_model: parameters, normalisation, and the range
+    in which the kernel trusts the model (outside it the heuristic decides): the
+    training range of every feature widened by `margin` of its span, and the
+    size features (log2) by LOG2_MARGIN more."""
     lo, hi = X.min(axis=0), X.max(axis=0)
     span = np.maximum(hi - lo, 1e-3)
-    return np.concatenate([theta, mean, istd, lo - margin * span, hi + margin * span]).astype(
-        np.float32)
+    lo, hi = lo - margin * span, hi + margin * span
+    for i in LOG2_FEATURES:
+        lo[i] -= LOG2_MARGIN
+        hi[i] += LOG2_MARGIN
+    return np.concatenate([theta, mean, istd, lo, hi]).astype(np.float32)
 
 
 def save_blob(blob, path=MODEL_PATH):

@@ -231,7 +231,7 @@ def test_segmented_runs_match_single_launch():
                 assert len(log) == alpha
                 assert list(np.bincount([r.variant for r in log], minlength=3)) == \
                     list(s["rounds_by_variant"])
-                t.set_params(sched_commit_rounds=8, sched_recheck_rounds=64)
+                t.set_params(sched_commit_rounds=32, sched_recheck_rounds=128)
 
 
 def test_committed_stretches_on_a_deep_cascade():
