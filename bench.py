@@ -34,13 +34,17 @@ if ROOT not in sys.path:
 METRIC = "edges/s (m/trim time) at 1 GB300, % HBM roofline; learned/batched vs fixed schedule"
 UNIT = "edges/s"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trim_persistent_kernel_rmat22.txt")
+REFERENCE_BUDGET_S = 150.0  # wall-clock bound of the reference arm's timed steps
 KERNEL_SRC = os.path.join(ROOT, "paper_2107_12720_gb300", "csrc", "trim_kernels.cu")
 
 
 # ---------------------------------------------------------------- workload
 
-def workload(idx: int):
+def workload(idx: int, small: bool = False):
     import graphgen.configs as cfg
+    if small:  # the same recipe at the sizes of the parity tests (profiling captures)
+        g = cfg.config_small(idx)
+        return g, f"small case of config {idx}: {g.name} (n={g.n}, m={g.m})"
     g = cfg.config(idx)
     names = {0: "planted_trim n=100,000 (C 30k / R 30k / T 40k), seed 1",
              1: "rmat22: R-MAT scale 22 (n=4,194,304), edge factor 16, a/b/c=.57/.19/.19, "
@@ -128,6 +132,32 @@ def algorithmic_bytes(n: int, st: dict, variant_flags: dict) -> int:
     b += 24 * st["candidates"]
     b += 8 * st["edges_inspected"]
     return int(b)
+
+
+def atomic_ceiling(P, t, off_in, tgt_in, pushed: int, cap: int = 32 << 20):
+    """L2 atomic ceiling of the AC-4 pushes of the last run: the counter indices
+    the run decremented (the in-edges of its removed vertices, at most `cap` of
+    them, in removal-agnostic vertex order) replayed by one fully parallel kernel
+    of returning atomicSub (trim_probe_atomic_rate). Returns (ops/s, indices)."""
+    import torch
+    if pushed <= 0:
+        return None, 0
+    lvl = t.level(device=False)
+    dead = np.nonzero(lvl != P.TRIM_LIVE)[0]
+    starts = off_in[dead].astype(np.int64)
+    lens = off_in[dead + 1].astype(np.int64) - starts
+    keep = np.searchsorted(np.cumsum(lens), cap, side="right")
+    starts, lens = starts[:keep], lens[:keep]
+    total = int(lens.sum())
+    if total == 0:
+        return None, 0
+    shift = np.repeat(starts - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)
+    idx = tgt_in[np.arange(total, dtype=np.int64) + shift].astype(np.uint32)
+    d_idx = torch.from_numpy(idx.view(np.int32)).cuda()
+    d_cnt = torch.empty(len(lvl), dtype=torch.int32, device="cuda")
+    ms = P.abi.trim_probe_atomic_rate(d_idx.data_ptr(), total, d_cnt.data_ptr(), len(lvl), 5,
+                                      torch.cuda.current_stream().cuda_stream)
+    return total / (ms * 1e-3), total
 
 
 def measured_peaks():
@@ -241,8 +271,21 @@ def run_reference(args, rank, ws):
     if rank != 0:
         return
     import oracle
-    g, wname = workload(args.config)
+    g, wname = workload(args.config, args.small)
     oi, ti = oracle.transpose(g.off, g.tgt)
+    # each step is one oracle run over the workload graph; when the requested
+    # steps would take longer than REFERENCE_BUDGET_S, each step is a run over
+    # the small graph of the same recipe instead (stated in the sample)
+    t0 = time.perf_counter()
+    oracle.peel(g.off, g.tgt, (oi, ti))
+    t_one = time.perf_counter() - t0
+    sample = f"the full workload graph per step, {args.steps} steps"
+    if t_one * (args.steps + args.warmup) > REFERENCE_BUDGET_S and not args.small:
+        import graphgen.configs as cfg
+        g = cfg.config_small(args.config)
+        oi, ti = oracle.transpose(g.off, g.tgt)
+        sample = (f"per step one run over the small graph of the same recipe ({g.name}, "
+                  f"m={g.m}): the full graph takes {t_one:.1f} s per run")
     for _ in range(args.warmup):
         oracle.peel(g.off, g.tgt, (oi, ti))
     t0 = time.perf_counter()
@@ -256,8 +299,7 @@ def run_reference(args, rank, ws):
             "data": "synthetic",
             "config": {"workload": wname, "n": g.n, "m": g.m},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"the full workload graph per step, {args.steps} steps",
-                             "cpu": cpu_name(), "nproc": os.cpu_count()},
+                             "sample": sample, "cpu": cpu_name(), "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -351,7 +393,7 @@ def run_ours(args, rank, ws, local):
     import torch
     import paper_2107_12720_gb300 as P
     torch.cuda.set_device(local)
-    g, wname = workload(args.config)
+    g, wname = workload(args.config, args.small)
     off_in, tgt_in = host_transpose(g.off, g.tgt)
     dev = lambda a: torch.from_numpy(a.view(np.int32)).cuda()
     d_off, d_tgt, d_oi, d_ti = dev(g.off), dev(g.tgt), dev(off_in), dev(tgt_in)
@@ -410,6 +452,9 @@ def run_ours(args, rank, ws, local):
                "copy_inputs_value": evc * ws,
                "copy_inputs": "same calls with the CSR first copied to device memory "
                               "(TRIM_MEM_HOST)"}
+    rate, probed = None, 0
+    if rank == 0 and st["in_edges_pushed"] and not args.no_atomic_probe:
+        rate, probed = atomic_ceiling(P, t, off_in, tgt_in, st["in_edges_pushed"])
     t.close()
     if rank != 0:
         return
@@ -432,7 +477,13 @@ def run_ours(args, rank, ws, local):
                      "frac": achieved / peak, "traffic": profiled_traffic(),
                      "kernel": "trim_persistent_kernel", "kernel_ms": kernel_ms,
                      "algorithmic_bytes": alg, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-                     if peak_kind == "measured" else "fallback 6.8 TB/s"},
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "l2_atomics": None if rate is None else {
+                         "ops": st["in_edges_pushed"], "ceiling_ops_per_s": rate,
+                         "ceiling_ms": st["in_edges_pushed"] / rate * 1e3,
+                         "share_of_kernel_ms": st["in_edges_pushed"] / rate * 1e3 / kernel_ms,
+                         "probe": f"trim_probe_atomic_rate: returning atomicSub on the run's own "
+                                  f"counter indices ({probed} of them), one fully parallel kernel"}},
     }
     if sweep:
         line["variants"] = sweep
@@ -466,6 +517,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--variant", default=None)
+    ap.add_argument("--small", action="store_true",
+                    help="the small case of --config (parity-test size), for profiling")
     ap.add_argument("--no-sweep", dest="sweep", action="store_false",
                     help="skip timing every variant next to the headline schedule")
     ap.add_argument("--sweep-variants", default="", help="comma-separated subset for --sweep")
@@ -473,6 +526,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-atomic-probe", action="store_true",
+                    help="skip measuring the L2 atomic ceiling of the run's pushes")
     ap.add_argument("--per-graph", type=int, default=0,
                     help="batched workload: also time each graph alone (N>0: a sample of N graphs, "
                          "-1: all)")

@@ -238,8 +238,8 @@ void trim_destroy(trim_ctx* ctx);
  * exercise out-of-memory paths without exhausting the device. */
 trim_err_t trim_set_alloc_limit(uint64_t bytes);
 
-/* Message of the last failed call on ctx (or of the last failed trim_create when
- * ctx is NULL). Never NULL. */
+/* Message of the last failed call on ctx (with ctx NULL: of the last failed
+ * call that takes no context, such as trim_create). Never NULL. */
 const char* trim_last_error(const trim_ctx* ctx);
 
 /* ---- scheduler MLP training kernels (plain fp32, no tensor cores) ----
@@ -261,6 +261,22 @@ trim_err_t trim_mlp_loss_grad(const float* params, const float* X, const uint8_t
                               float* loss, float* grad, void* scratch, void* cuda_stream);
 trim_err_t trim_mlp_adam_step(float* params, const float* grad, float* m, float* v, uint32_t t,
                               float lr, float beta1, float beta2, float eps, void* cuda_stream);
+
+/* ---- Diagnostic: the device's L2 atomic ceiling (no counterpart in the paper) ----
+ * AC-4 issues one returning atomicSub per in-edge it pushes; on large frontiers
+ * its time is bound by how many such atomics the L2 completes per second, not
+ * by DRAM bandwidth. trim_probe_atomic_rate measures that ceiling for a given
+ * stream of counter indices: it sets counters[0..n_counters) to 0xFFFFFFFF and
+ * runs one fully parallel kernel that applies atomicSub(&counters[idx[i]], 1)
+ * for i in [0, n_idx) and keeps the returned values (as AC-4 does), timed with
+ * CUDA events on cuda_stream; the kernel runs `reps` times and *ms_out receives
+ * the fastest. idx (n_idx values, each < n_counters) and counters are DEVICE
+ * pointers owned by the caller; counters is overwritten. Waits for the stream.
+ * Errors: TRIM_ERR_INVALID_ARG for null pointers, n_idx = 0, n_counters = 0 or
+ * reps = 0; TRIM_ERR_CUDA if a launch fails. */
+trim_err_t trim_probe_atomic_rate(const uint32_t* idx, uint64_t n_idx, uint32_t* counters,
+                                  uint32_t n_counters, uint32_t reps, void* cuda_stream,
+                                  float* ms_out);
 
 /* ---- Trimming without any device allocation (no counterpart in the paper) ----
  * For callers that cannot call cudaMalloc when they need a result: processes

@@ -87,6 +87,8 @@ SIGNATURES = [
     ("trim_mlp_loss_grad", _I, [_P, _P, _P, _U32, _P, _P, _P, _P]),
     ("trim_mlp_adam_step", _I, [_P, _P, _P, _P, _U32, _F, _F, _F, _F, _P]),
     ("trim_run_ac4_noalloc", _I, [_P, _P, _P, _P, _U32, _U32, _P, ctypes.POINTER(_U32), _P]),
+    ("trim_probe_atomic_rate", _I, [_P, ctypes.c_uint64, _P, _U32, _U32, _P,
+                                    ctypes.POINTER(ctypes.c_float)]),
 ]
 
 _lib = None
@@ -252,3 +254,12 @@ def trim_run_ac4_noalloc(offsets, targets, in_offsets, in_targets, n: int, m: in
     if rc != 0:
         raise TrimError(rc, "trim_run_ac4_noalloc failed")
     return int(rounds.value)
+
+
+def trim_probe_atomic_rate(idx, n_idx: int, counters, n_counters: int, reps: int, stream) -> float:
+    """Fastest of `reps` fully parallel passes of returning atomicSub over the
+    counter indices idx (device); counters (device) is overwritten. Returns ms."""
+    ms = ctypes.c_float(0.0)
+    check(lib().trim_probe_atomic_rate(_ptr(idx), n_idx, _ptr(counters), n_counters, reps, stream,
+                                       ctypes.byref(ms)), None)
+    return float(ms.value)

@@ -1022,4 +1022,39 @@ trim_err_t trim_set_alloc_limit(uint64_t bytes) {
   return TRIM_OK;
 }
 
+trim_err_t trim_probe_atomic_rate(const uint32_t* idx, uint64_t n_idx, uint32_t* counters,
+                                  uint32_t n_counters, uint32_t reps, void* cuda_stream,
+                                  float* ms_out) {
+  trim_ctx* c = nullptr;  // errors go to the context-free message
+  if (!idx || !counters || !ms_out || n_idx == 0 || n_counters == 0 || reps == 0)
+    return fail(c, TRIM_ERR_INVALID_ARG, "null pointer or zero size");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 3.0e38f;
+  cudaError_t e = cudaSuccess;
+  for (uint32_t r = 0; r < reps && e == cudaSuccess; ++r) {
+    e = cudaMemsetAsync(counters, 0xFF, (size_t)n_counters * 4, st);
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    if (e == cudaSuccess) {
+      trim_probe_atomic_kernel<<<sms * 32, 256, 0, st>>>(idx, n_idx, counters);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess) best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(c, e, "trim_probe_atomic_rate");
+  *ms_out = best;
+  return TRIM_OK;
+}
+
 }  // extern "C"

@@ -136,3 +136,15 @@ __global__ void trim_validate_batch_kernel(const uint32_t* off, const uint32_t* 
       if (vgraph[tgt[k]] != g) atomicOr(bad, 4u);
   }
 }
+
+// Diagnostic: returning atomicSub over an index stream, fully parallel. The
+// returned values are folded into `acc` so the atomics keep their return path
+// (the form AC-4 uses); the guarded store never fires for counters that start
+// at 0xFFFFFFFF and are decremented at most 2^32 - 2 times.
+__global__ void trim_probe_atomic_kernel(const uint32_t* idx, uint64_t n, uint32_t* counters) {
+  uint32_t acc = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    acc |= (atomicSub(&counters[idx[i]], 1u) == 0u) ? 1u : 0u;
+  if (acc) counters[0] = 0u;
+}

@@ -185,6 +185,7 @@ __device__ __forceinline__ void set_error(const Dev& D, unsigned code, unsigned 
 }  // namespace trimk
 
 // kernels (trim_kernels.cu, one flavour per variant set; trim_aux.cu), launched from trim_api.cu
+__global__ void trim_probe_atomic_kernel(const uint32_t* idx, uint64_t n, uint32_t* counters);
 __global__ void trim_persistent_kernel_m1(trimk::Dev D);   // AC-4 only
 __global__ void trim_persistent_kernel_m2(trimk::Dev D);   // AC-6 only
 __global__ void trim_persistent_kernel_m4(trimk::Dev D);   // AC-3 only

@@ -93,6 +93,14 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     assert rc == 8, rc  # TRIM_ERR_NO_DEVICE
 
 
+def test_atomic_probe_rejects_bad_args(lib):
+    ms = ctypes.c_float()
+    assert lib.trim_probe_atomic_rate(None, 1, None, 1, 1, None, ctypes.byref(ms)) == 1
+    buf = (ctypes.c_uint32 * 4)()
+    assert lib.trim_probe_atomic_rate(buf, 0, buf, 4, 1, None, ctypes.byref(ms)) == 1
+    assert lib.trim_probe_atomic_rate(buf, 4, buf, 4, 0, None, ctypes.byref(ms)) == 1
+
+
 def test_mlp_entry_points_reject_bad_args(lib):
     assert lib.trim_mlp_forward(None, None, 0, None, None) == 1
     assert lib.trim_mlp_loss_grad(None, None, None, 0, None, None, None, None) == 1

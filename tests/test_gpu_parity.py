@@ -423,3 +423,21 @@ def test_full_large_mixed_workload_certificate():
             np.testing.assert_array_equal(blk[nC + nR:], np.arange(nT, dtype=np.uint32) // chains)
             assert s["rounds"] == int(lvl[lvl != P.TRIM_LIVE].max()) + 1
         del lvl, st
+
+
+def test_atomic_probe_decrements_each_index_once_per_pass():
+    """trim_probe_atomic_rate: after the last pass every counter equals
+    0xFFFFFFFF minus the number of times its index occurs; the time is > 0."""
+    import torch
+    P = _P()
+    rng = np.random.default_rng(5)
+    n_cnt = 1000
+    idx = rng.integers(0, n_cnt, 200000).astype(np.uint32)
+    d_idx = torch.from_numpy(idx.view(np.int32)).cuda()
+    d_cnt = torch.zeros(n_cnt, dtype=torch.int32, device="cuda")
+    ms = P.abi.trim_probe_atomic_rate(d_idx.data_ptr(), idx.size, d_cnt.data_ptr(), n_cnt, 3,
+                                      torch.cuda.current_stream().cuda_stream)
+    assert ms > 0
+    got = d_cnt.cpu().numpy().view(np.uint32)
+    want = (0xFFFFFFFF - np.bincount(idx, minlength=n_cnt)).astype(np.uint32)
+    assert np.array_equal(got, want)
