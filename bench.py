@@ -407,7 +407,9 @@ def run_ours(args, rank, ws, local):
     # the plain variants are the measured schedules of the single-graph
     # workloads; the large mixed graph runs the learned scheduler
     headline = args.variant or ("learned" if (args.config == 4 and have_model) else "ac4")
-    batched = g.graph_off is not None
+    # the batched workload is a packed set of independent graphs; the large
+    # mixed graph is also a union of parts, but one graph to trim
+    batched = g.graph_off is not None and args.config == 3
     gofs = g.graph_off if batched else None
 
     sweep = {}

@@ -200,9 +200,10 @@ trim_err_t trim_level_device_ptr(const trim_ctx* ctx, const uint32_t** out);
  * graph g owns vertices [graph_off[g], graph_off[g+1]) and no edge may cross two
  * graphs (checked with TRIM_FLAG_VALIDATE). graph_off: G+1 host uint32 values,
  * graph_off[0]=0, graph_off[G]=n. The packed CSR is the disjoint union of the
- * graphs, so all of them are trimmed by one persistent launch of `variant`
- * (captured into a CUDA graph and replayed from the second call with the same
- * variant on): every round serves every graph still peeling. Results equal
+ * graphs, so all of them are trimmed together: every round serves every graph
+ * still peeling. A fixed variant is one persistent launch, captured into a
+ * CUDA graph on the second call with the same variant and replayed from then
+ * on; a scheduled variant runs as trim_run runs it (segments). Results equal
  * trimming each graph alone: read them with trim_status / trim_level. */
 trim_err_t trim_batch_run(trim_ctx* ctx, const uint32_t* graph_off, uint32_t G,
                           trim_variant_t variant, trim_run_stats_t* stats);

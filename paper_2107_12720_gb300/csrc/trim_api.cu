@@ -769,17 +769,15 @@ trim_err_t enqueue_batch(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
                          trim_variant_t variant) {
   (void)graph_off;
   (void)G;
+  if (c->n == 0) return enqueue_run(c, variant);  // nothing to launch, nothing to capture
   if (c->batch_exec == nullptr || c->batch_variant != (int)variant) {
     // the first call with a variant runs directly (a one-shot caller pays no
-    // capture); the second captures, then every later call replays the graph.
-    // The direct run also builds G^T if needed and leaves all allocations in
-    // place before the capture.
+    // capture; it also builds G^T if needed and makes every allocation the run
+    // needs); the second captures the launch, then launches and replays it.
     if (c->batch_last_variant != (int)variant) {
       c->batch_last_variant = (int)variant;
       return enqueue_run(c, variant);
     }
-    TRY(enqueue_run(c, variant));
-    TRY(finish_run(c, nullptr));
     if (c->batch_exec) {
       cudaGraphExecDestroy(c->batch_exec);
       c->batch_exec = nullptr;
@@ -873,6 +871,10 @@ trim_err_t trim_batch_run(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
       return fail(c, TRIM_ERR_INVALID_ARG, "graph_off must be non-decreasing");
   if (c->flags & TRIM_FLAG_VALIDATE) TRY(validate_batch(c, graph_off, G));
   c->last_segments = 1;
+  // a scheduled variant hands the run between kernels from the host
+  // (segments), which a captured graph cannot do: it runs as trim_run does
+  if (variant >= TRIM_SCHED_HEURISTIC && variant <= TRIM_SCHED_SCRIPTED)
+    return run_segmented(c, variant, stats);
   TRY(enqueue_batch(c, graph_off, G, variant));
   return finish_run(c, stats);
 }

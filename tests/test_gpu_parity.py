@@ -359,7 +359,7 @@ def test_batch_run_matches_oracle_and_per_graph_runs():
     lvl, st, alpha = oracle.peel(u.off, u.tgt)
     off, tgt = dev_csr(u)
     with P.Trimmer(off, tgt, flags=P.TRIM_FLAG_VALIDATE) as t:
-        for v in ["ac4", "heuristic", "ac4", "ac6", "ac3"]:
+        for v in ["ac4", "heuristic", "ac4", "ac6", "ac3", "learned"]:
             for _ in range(3):
                 s = t.batch_run(u.graph_off, v)
                 check(t, lvl, st, alpha, f"batch-{v}", s)
