@@ -172,10 +172,11 @@ def kernel_source_sha() -> str:
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(config: int, small: bool, schedule: str):
     """DRAM bytes per launch of the persistent kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    if not os.path.exists(PROFILE_TRAFFIC):
+    summary, if it covers this run (the rmat22 workload, AC-4) and was taken on
+    the current kernel source; else None."""
+    if config != 1 or small or schedule != "ac4" or not os.path.exists(PROFILE_TRAFFIC):
         return None
     kv = {}
     for line in open(PROFILE_TRAFFIC):
@@ -476,7 +477,7 @@ def run_ours(args, rank, ws, local):
         "e2e": e2e,
         "gpu_launches": st["launches"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.config, args.small, headline),
                      "kernel": "trim_persistent_kernel", "kernel_ms": kernel_ms,
                      "algorithmic_bytes": alg, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
