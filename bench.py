@@ -308,6 +308,20 @@ def run_reference(args, rank, ws):
 
 # ---------------------------------------------------------------- GPU arm
 
+def apply_tuned(t, args, variant):
+    """Autotuned trim_params_t of this workload and variant (the autotuner's
+    result file), unless --no-tuned or none were tuned; returns them."""
+    if args.no_tuned:
+        return {}
+    from paper_2107_12720_gb300 import autotune
+    return autotune.apply(t, f"config{args.config}{'-small' if args.small else ''}", variant)
+
+
+def restore_defaults(t):
+    from paper_2107_12720_gb300 import autotune
+    t.set_params(**autotune.default_params())
+
+
 def time_variant(P, t, variant, steps, warmup, flush_buf, graph_off=None):
     """Device time of `steps` complete trims (L2 flushed before each). With
     graph_off the step is one batched trim (trim_batch_run, a replayed CUDA
@@ -366,7 +380,7 @@ def per_graph_fixed(P, g, variant="ac4", limit=None):
     return total_ms * scale, count
 
 
-def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None, mapped=True):
+def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None, mapped=True, params=None):
     """Through the C ABI with host buffers, host wall clock around the whole
     call sequence: trim_create on page-locked host CSR (and G^T), trim_run,
     trim_level into a host array, trim_destroy. mapped: the kernels read the
@@ -381,6 +395,8 @@ def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None, mapped=Tru
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with P.Trimmer(ho, ht, hoi, hti, host_mapped=mapped) as t:
+            if params:
+                t.set_params(**params)
             t.batch_run(graph_off, variant) if graph_off is not None else t.run(variant)
             P.trim_level(t.ctx, out.data_ptr(), 0)
         t1 = time.perf_counter()
@@ -418,15 +434,19 @@ def run_ours(args, rank, ws, local):
         names = args.sweep_variants.split(",") if args.sweep_variants else \
             ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if have_model else [])
         for v in names:
+            tuned_v = apply_tuned(t, args, v)
             ts, ks, st = time_variant(P, t, v, max(args.sweep_steps, args.steps // 10), 1, flush,
                                       gofs)
+            restore_defaults(t)
             sweep[v] = {"ms": statistics.mean(ts), "kernel_ms": statistics.mean(ks),
+                        "params": tuned_v or "defaults",
                         "edges_per_s": g.m / (statistics.mean(ts) * 1e-3),
                         "rounds_by_variant": st["rounds_by_variant"]}
             print(f"# {v:10s} {statistics.mean(ts):8.4f} ms  kernel {statistics.mean(ks):8.4f} ms"
                   f"  {g.m / statistics.mean(ts) / 1e-3:.3e} edges/s  rounds {st['rounds_by_variant']}",
                   file=sys.stderr, flush=True)
 
+    tuned = apply_tuned(t, args, headline)
     clocks = ClockSampler(local)
     if rank == 0:
         clocks.start()
@@ -446,8 +466,12 @@ def run_ours(args, rank, ws, local):
 
     e2e = None
     if rank == 0 and args.e2e_steps > 0:
-        ev, h2d, d2h = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs)
-        evc, _, _ = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs, False)
+        full = None
+        if tuned:
+            from paper_2107_12720_gb300 import autotune
+            full = {**autotune.default_params(), **tuned}
+        ev, h2d, d2h = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs, True, full)
+        evc, _, _ = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs, False, full)
         e2e = {"value": ev * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "inputs": "page-locked host CSR + G^T read in place by the kernels "
@@ -470,6 +494,7 @@ def run_ours(args, rank, ws, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wname, "n": g.n, "m": g.m, "schedule": headline,
                    "rounds": st["rounds"], "rounds_by_variant": st["rounds_by_variant"],
+                   "params": tuned or "library defaults",
                    "l2": "flushed before every step (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "timing": "CUDA events on the library stream around reset + persistent kernel"},
@@ -529,6 +554,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tuned", action="store_true",
+                    help="library default parameters instead of the autotuned ones")
     ap.add_argument("--no-atomic-probe", action="store_true",
                     help="skip measuring the L2 atomic ceiling of the run's pushes")
     ap.add_argument("--per-graph", type=int, default=0,

@@ -237,10 +237,12 @@ void default_params(trim_params_t* p) {
 
 // per-warp append slices in dynamic shared memory: 4 buffers (dead log, AC-4
 // work-list rows and edge offsets, AC-3 live list) of kSliceEntries words per
-// warp, sized for the largest block (512 threads = 16 warps)
+// warp of the block (64 KB for 512 threads)
 constexpr uint32_t kSliceEntries = 256;
 constexpr uint32_t kSbufCap = kSliceEntries;
-size_t dyn_smem_bytes() { return 16 * 4 * (size_t)kSliceEntries * sizeof(uint32_t); }
+size_t dyn_smem_bytes(uint32_t block_threads) {
+  return (block_threads / 32) * 4 * (size_t)kSliceEntries * sizeof(uint32_t);
+}
 
 // kernel flavours: index 0..3 = AC-4 only, AC-6 only, AC-3 only, everything;
 // 4..6 = AC-4, AC-6, AC-3 each with the per-round schedulers (segments)
@@ -274,10 +276,10 @@ trim_err_t compute_grid(trim_ctx* c) {
   for (int k = 0; k < kNumFlavours; ++k) {
     int per_sm = 0;
     CK(cudaFuncSetAttribute(kFlavours[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)dyn_smem_bytes()));
+                            (int)dyn_smem_bytes(512)));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kFlavours[k],
                                                      (int)c->params.block_threads,
-                                                     dyn_smem_bytes()));
+                                                     dyn_smem_bytes(c->params.block_threads)));
     if (per_sm <= 0) return fail(c, TRIM_ERR_INVALID_ARG, "block_threads does not fit on an SM");
     if (c->params.ctas_per_sm) per_sm = std::min<int>(per_sm, (int)c->params.ctas_per_sm);
     c->grids[k] = per_sm * c->sm_count;
@@ -621,7 +623,8 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   CK(cudaEventRecordWithFlags(c->ev0, c->stream, rec));
   void* args[] = {&D};
   CK(cudaLaunchCooperativeKernel((const void*)kFlavours[flavour], dim3(grid),
-                                 dim3(c->params.block_threads), args, dyn_smem_bytes(),
+                                 dim3(c->params.block_threads), args,
+                                 dyn_smem_bytes(c->params.block_threads),
                                  c->stream));
   CK(cudaEventRecordWithFlags(c->ev1, c->stream, rec));
   c->pending = true;
@@ -643,7 +646,8 @@ trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base, uint32_t 
   c->last_flavour = flavour;
   void* args[] = {&D};
   CK(cudaLaunchCooperativeKernel((const void*)kFlavours[flavour], dim3(c->grids[flavour]),
-                                 dim3(c->params.block_threads), args, dyn_smem_bytes(),
+                                 dim3(c->params.block_threads), args,
+                                 dyn_smem_bytes(c->params.block_threads),
                                  c->stream));
   CK(cudaEventRecord(c->ev1, c->stream));
   return TRIM_OK;
