@@ -7,7 +7,7 @@ For one workload it times every point of a small search space with the
 library's own device timer (median of `reps` complete runs after one warm-up)
 and keeps, per variant, the fastest point:
 
-  block_threads      256, 384, 512 threads per persistent CTA
+  block_threads      128, 256, 384, 512 threads per persistent CTA
   ctas_per_sm        as many as fit (0), or 1
   heur_push_ratio    0.5, 1, 2    (heuristic / learned fallback: AC-4 vs the rest)
   heur_ac6_ratio     0.5, 1, 2    (heuristic without G^T: AC-6 vs AC-3)
@@ -36,7 +36,8 @@ from . import scheduler as S  # noqa: E402
 
 TUNED_PATH = os.path.join(S.MODEL_DIR, "tuned_params.json")
 
-LAUNCH_SPACE = {"block_threads": (256, 384, 512), "ctas_per_sm": (0, 1)}
+LAUNCH_SPACE = {"block_threads": (128, 256, 384, 512), "ctas_per_sm": (0, 1)}
+MIN_GAIN = 0.02  # a point must beat the best so far by 2% (timing noise is ~0.5%)
 SCHED_SPACE = {"heur_push_ratio": (0.5, 1.0, 2.0), "heur_ac6_ratio": (0.5, 1.0, 2.0),
                "sched_commit_rounds": (16, 32, 64)}
 
@@ -73,7 +74,7 @@ def tune(trimmer, variants=("ac4", "ac6", "ac3", "heuristic", "learned"), reps=5
             ms = time_point(trimmer, v, p, reps)
             if log:
                 log(f"{v:9s} {p} {ms:.4f} ms")
-            if ms < best_ms:
+            if ms < best_ms * (1.0 - MIN_GAIN):
                 best, best_ms = p, ms
         if v == "ac4":
             best_launch = dict(best)
@@ -84,7 +85,7 @@ def tune(trimmer, variants=("ac4", "ac6", "ac3", "heuristic", "learned"), reps=5
                 ms = time_point(trimmer, v, q, reps)
                 if log:
                     log(f"{v:9s} {q} {ms:.4f} ms")
-                if ms < best_ms:
+                if ms < best_ms * (1.0 - MIN_GAIN):
                     best, best_ms = q, ms
         out[v] = {"params": best, "ms": best_ms, "default_ms": default_ms}
     trimmer.set_params(**default_params())

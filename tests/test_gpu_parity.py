@@ -441,3 +441,15 @@ def test_atomic_probe_decrements_each_index_once_per_pass():
     got = d_cnt.cpu().numpy().view(np.uint32)
     want = (0xFFFFFFFF - np.bincount(idx, minlength=n_cnt)).astype(np.uint32)
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("block,cps", [(256, 0), (384, 0), (512, 1), (128, 1)])
+def test_launch_shapes_give_identical_results(block, cps):
+    """Every launch shape the autotuner may pick gives the oracle's levels."""
+    P = _P()
+    g = cfg.config_small(1)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    with P.Trimmer(g.off, g.tgt) as t:
+        t.set_params(block_threads=block, ctas_per_sm=cps)
+        for v in VARIANTS:
+            check(t, lvl, st, alpha, f"{v}-{block}x{cps}", t.run(v))
