@@ -169,7 +169,11 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    """Hash of the kernel source's code: comment-only lines and blank lines are
+    left out, so that editing a comment does not orphan a profile."""
+    lines = [ln.rstrip() for ln in open(KERNEL_SRC, encoding="utf-8")]
+    code = "\n".join(ln for ln in lines if ln.strip() and not ln.strip().startswith("//"))
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def profiled_traffic(config: int, small: bool, schedule: str):

@@ -25,9 +25,15 @@
 // Rounds end at a grid-wide barrier (a monotone arrival counter, bounded spin).
 // No CTA hands anything to another between rounds: every CTA advances its own
 // copy of the schedule state (Sched, in shared memory) from the same global
-// inputs, so the copies agree. Appends to the dead log and to the AC-3 live
-// list go to per-CTA shared-memory buffers and reach global memory with one
-// atomic per CTA per round.
+// inputs, so the copies agree. Appends to the dead log, the AC-4 work list and
+// the AC-3 live list go to per-warp shared-memory slices and reach global
+// memory with one atomic per counter per CTA per round.
+//
+// A scheduled run may span several launches (segments): at the start of a
+// round every CTA can decide from the same state to stop (the kernel lacks the
+// chosen variant, the scheduler committed to its choice, or the host asked for
+// the run back at that round); CTA 0 then saves the schedule state in the
+// control block, and the next launch resumes from it at the same round.
 #include "trim_internal.cuh"
 
 // This file is compiled once per kernel flavour: TRIM_MODES is a bit set of the
