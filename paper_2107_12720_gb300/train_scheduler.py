@@ -36,7 +36,7 @@ from paper_2107_12720_gb300 import scheduler as S  # noqa: E402
 
 def training_graphs(quick=False):
     """The benchmark families at other seeds and sizes (never the evaluation
-    graphs): R-MAT scale 15..21 with several sink shares and skews, planted
+    graphs): R-MAT scale 15..22 with several sink shares and skews, planted
     graphs of 1e5 and 1e6 vertices, deep cascades of 2^15..2^21 vertices and
     45..720 rounds, small batches and small mixed graphs."""
     gs = [cfg.rmat22(seed=101, scale=16), cfg.rmat22(seed=102, scale=17),
@@ -53,7 +53,9 @@ def training_graphs(quick=False):
           cfg.deep_cascade(seed=113, log2n=20, n_chains=4096),
           cfg.deep_cascade(seed=114, log2n=21, n_chains=2048),
           cfg.batched(seed=115, G=1024, median=1000.0, nmin=16, nmax=200000),
-          cfg.large_mixed(seed=116, scale=18, block_log2=18, chain_len=500)]
+          cfg.large_mixed(seed=116, scale=18, block_log2=18, chain_len=500),
+          cfg.rmat22(seed=117, scale=22),
+          graphgen.rmat(118, 22, 12, 0.55, 0.2, 0.2, 0.2, name="rmat22-ef12-sinks20")]
     return gs[:4] if quick else gs
 
 
