@@ -9,8 +9,10 @@
  * Conventions shared by every entry point:
  *  - Every call returns a trim_err_t; nothing aborts. A failed call leaves the
  *    caller's output buffers untouched; trim_last_error() describes it.
- *  - Vertex ids and CSR offsets are uint32. n <= 0xFFFFFFFE (0xFFFFFFFF is the
- *    LIVE sentinel of trim_level), m < 2^32.
+ *  - Vertex ids and CSR offsets are uint32: n <= 2^31 vertices (so that no
+ *    grid-stride index can wrap) and m <= 2^32 - 64 edges (so that 32-edge
+ *    chunk arithmetic cannot wrap); 0xFFFFFFFF is the LIVE sentinel of
+ *    trim_level.
  *  - Device pointers passed in are BORROWED: they must stay valid and unchanged
  *    until trim_destroy(). Host pointers are copied during the call.
  *  - A context is bound to one CUDA stream and to the device current at

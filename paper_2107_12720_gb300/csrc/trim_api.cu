@@ -429,8 +429,8 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
   if (g->on_device < TRIM_MEM_HOST || g->on_device > TRIM_MEM_HOST_MAPPED ||
       (gi && (gi->on_device < TRIM_MEM_HOST || gi->on_device > TRIM_MEM_HOST_MAPPED)))
     return fail(c, TRIM_ERR_INVALID_ARG, "on_device must be one of TRIM_MEM_*");
-  if (g->n > 0xFFFFFFFEu || g->m >= (1ull << 32))
-    return fail(c, TRIM_ERR_TOO_LARGE, "n must be < 2^32-1 and m < 2^32");
+  if (g->n > (1u << 31) || g->m > (1ull << 32) - 64)
+    return fail(c, TRIM_ERR_TOO_LARGE, "n must be <= 2^31 and m <= 2^32 - 64");
   if (g->offsets == nullptr || (g->m && g->targets == nullptr))
     return fail(c, TRIM_ERR_INVALID_ARG, "csr_out: null array");
   if (gi) {

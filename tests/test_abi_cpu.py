@@ -61,6 +61,11 @@ def test_host_argument_checks_without_device(lib):
     # m too large for uint32 offsets
     big = TrimCsr(2, 1 << 33, off.ctypes.data, tgt.ctypes.data, 0)
     assert lib.trim_create(ctypes.byref(big), None, None, 0, ctypes.byref(ctx)) == 3
+    # limits that keep every index computation from wrapping: n <= 2^31, m <= 2^32 - 64
+    big = TrimCsr((1 << 31) + 1, 2, off.ctypes.data, tgt.ctypes.data, 0)
+    assert lib.trim_create(ctypes.byref(big), None, None, 0, ctypes.byref(ctx)) == 3
+    big = TrimCsr(2, (1 << 32) - 63, off.ctypes.data, tgt.ctypes.data, 0)
+    assert lib.trim_create(ctypes.byref(big), None, None, 0, ctypes.byref(ctx)) == 3
     # offsets inconsistent with m (host check)
     bad = TrimCsr(2, 3, off.ctypes.data, tgt.ctypes.data, 0)
     assert lib.trim_create(ctypes.byref(bad), None, None, 0, ctypes.byref(ctx)) == 2
