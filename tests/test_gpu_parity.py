@@ -138,6 +138,15 @@ def test_host_mapped_inputs(i):
     with P.Trimmer(pin(g.off), pin(g.tgt), host_mapped=True) as t:
         for v in ["ac6", "ac4"]:
             check(t, lvl, st, alpha, "mapped-noGT-" + v, t.run(v))
+        # outputs into page-locked host buffers, aligned and not
+        out = torch.empty(g.n + 4, dtype=torch.int32).pin_memory()
+        for o in (0, 1):
+            out.fill_(7)
+            P.trim_level(t.ctx, out.data_ptr() + 4 * o, 0)
+            assert np.array_equal(out.numpy()[o:o + g.n].view(np.uint32), lvl)
+        so = torch.empty(g.n + 3, dtype=torch.uint8).pin_memory()
+        P.trim_status(t.ctx, so.data_ptr() + 3, 0)
+        assert np.array_equal(so.numpy()[3:], st)
 
 
 def test_host_mapped_pageable_or_refused():
