@@ -53,7 +53,6 @@ struct trim_ctx {
   uint8_t* status_tmp = nullptr;
   trim_params_t params{};
   int grids[7] = {0, 0, 0, 0, 0, 0, 0};
-  int last_flavour = 3;
   trimk::Dev last_dev{};        // arguments of the last launch (segments reuse them)
   int seg_first[3] = {-1, -1, -1};  // per scheduled mode: flavour of its last first round
   uint64_t last_segments = 0;       // kernel launches of the last trim_run
@@ -63,11 +62,9 @@ struct trim_ctx {
   bool capturing = false;
   int batch_variant = -1;
   int batch_last_variant = -1;
-  uint64_t batch_graph_launches = 0;
   bool ran = false;
   bool pending = false;
   bool s_cnt_dirty = false;
-  uint32_t last_mode = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err = "no error";
   trim_run_stats_t last{};
@@ -576,7 +573,6 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   if (c->n == 0) {
     c->ran = true;
     c->pending = false;
-    c->last_mode = variant;
     std::memset(c->h_ctrl, 0, sizeof(Ctrl));
     CK(cudaEventRecord(c->ev0, c->stream));
     CK(cudaEventRecord(c->ev1, c->stream));
@@ -611,7 +607,6 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   int flavour = kFlavourAll;
   if (variant <= TRIM_AC3_PULL) flavour = (int)variant;
   else if (seg_flavour >= 0) flavour = seg_flavour;
-  c->last_flavour = flavour;
   c->last_dev = D;
   const int grid = c->grids[flavour];
   if ((uint32_t)grid > 8192) return fail(c, TRIM_ERR_INVALID_ARG, "grid too large");
@@ -628,7 +623,6 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
                                  c->stream));
   CK(cudaEventRecordWithFlags(c->ev1, c->stream, rec));
   c->pending = true;
-  c->last_mode = variant;
   c->ran = false;
   return TRIM_OK;
 }
@@ -643,7 +637,6 @@ trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base, uint32_t 
   D.bar_base = bar_base;
   D.mode = mode;
   D.stop_round = stop_round;
-  c->last_flavour = flavour;
   void* args[] = {&D};
   CK(cudaLaunchCooperativeKernel((const void*)kFlavours[flavour], dim3(c->grids[flavour]),
                                  dim3(c->params.block_threads), args,
@@ -819,7 +812,6 @@ trim_err_t enqueue_batch(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
   CK(cudaGraphLaunch(c->batch_exec, c->stream));
   c->pending = true;
   c->ran = false;
-  c->batch_graph_launches++;
   return TRIM_OK;
 }
 
