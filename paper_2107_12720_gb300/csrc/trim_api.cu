@@ -35,7 +35,7 @@ struct trim_ctx {
   const uint32_t* tgt = nullptr;
   const uint32_t* ioff = nullptr;
   const uint32_t* itgt = nullptr;
-  std::vector<void*> owned;  // every cudaMalloc of this context
+  std::vector<void*> owned;  // every device allocation of this context (library pool)
   uint64_t allocated = 0;
   uint32_t *level = nullptr, *cnt = nullptr, *supp = nullptr, *s_head = nullptr,
            *s_next = nullptr, *s_cnt = nullptr, *s_off = nullptr, *s_list = nullptr,
@@ -52,7 +52,7 @@ struct trim_ctx {
   uint32_t script_len = 0;
   uint8_t* status_tmp = nullptr;
   trim_params_t params{};
-  int grids[7] = {0, 0, 0, 0, 0, 0, 0};
+  int grids[7] = {0, 0, 0, 0, 0, 0, 0};  // cooperative grid size of each kernel flavour
   trimk::Dev last_dev{};        // arguments of the last launch (segments reuse them)
   int seg_first[3] = {-1, -1, -1};  // per scheduled mode: flavour of its last first round
   uint64_t last_segments = 0;       // kernel launches of the last trim_run
