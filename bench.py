@@ -443,6 +443,8 @@ def run_ours(args, rank, ws, local):
                                       gofs)
             restore_defaults(t)
             sweep[v] = {"ms": statistics.mean(ts), "kernel_ms": statistics.mean(ks),
+                        "ms_ci95": (1.96 * statistics.stdev(ts) / len(ts) ** 0.5)
+                        if len(ts) > 1 else None,
                         "params": tuned_v or "defaults",
                         "edges_per_s": g.m / (statistics.mean(ts) * 1e-3),
                         "rounds_by_variant": st["rounds_by_variant"]}
@@ -494,7 +496,9 @@ def run_ours(args, rank, ws, local):
     achieved = alg / (kernel_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "ms_per_step_ci95": (1.96 * statistics.stdev(ts) / len(ts) ** 0.5) if len(ts) > 1 else None,
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wname, "n": g.n, "m": g.m, "schedule": headline,
                    "rounds": st["rounds"], "rounds_by_variant": st["rounds_by_variant"],
