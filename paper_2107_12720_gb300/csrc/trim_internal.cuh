@@ -36,7 +36,8 @@ struct RoundStat {
   unsigned long long sum_out;  // sum of out-degrees of F_r
   unsigned int hist[3];        // in-degree < 8, < 256, >= 256
   unsigned int live_count;     // AC-3: survivors written to the output live list in round r
-  unsigned int pad[2];
+  unsigned int max_din;        // largest in-degree among the work-list entries of F_r
+  unsigned int pad;
 };
 
 // The schedule state of the current round. Every CTA keeps its own copy in
@@ -59,6 +60,7 @@ struct Sched {
   uint32_t mixed;         // 1 once a round ran AC-6 or AC-3 (AC-4 must then re-check levels)
   uint32_t vcount[3];     // rounds run so far by AC-4, AC-6, AC-3
   uint32_t stable;        // rounds in a row the scheduler kept its choice (0 outside schedulers)
+  uint32_t bmax;          // largest in-degree among work-list entries AC-4 has not pushed
   unsigned long long m_live;     // out-edges of live vertices
   float feat[12];                // features that chose this round's variant
 };

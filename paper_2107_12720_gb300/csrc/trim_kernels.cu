@@ -86,6 +86,7 @@ struct WarpSlice {
   uint32_t log_base, w4_base, edge_base, live_base;  // global bases at the CTA flush
   uint32_t sum_in, sum_out;  // feature sums (distinct removed vertices: at most m < 2^32)
   uint32_t hist[3];
+  uint32_t max_din;          // largest in-degree among this warp's work-list entries
 };
 
 // Per-CTA shared state.
@@ -249,10 +250,14 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
     slice(warp, 0)[pl + __popc(mask & lt)] = u;
     D.level[u] = r;
   }
-  if (w) {
-    const unsigned at = pw + __popc(wmask & lt);
-    w4_rows(B, warp)[at] = row;
-    slice(warp, 2)[at] = pe + eincl - ew;
+  unsigned mdin = 0;
+  if (wmask) {
+    mdin = __reduce_max_sync(FULL, ew);
+    if (w) {
+      const unsigned at = pw + __popc(wmask & lt);
+      w4_rows(B, warp)[at] = row;
+      slice(warp, 2)[at] = pe + eincl - ew;
+    }
   }
   unsigned s_in = 0, s_out = 0;
   unsigned h0 = 0, h1 = 0;
@@ -268,6 +273,7 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
     ws.ncount += k - kl;
     ws.nw4 = pw + kw;
     ws.nedge = pe + esum;
+    ws.max_din = max(ws.max_din, mdin);
     if (live_edges) ws.sum_out += s_out;
     if (feats) {
       ws.sum_in += s_in;
@@ -333,6 +339,10 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
       const uint32_t s_out = __reduce_add_sync(FULL, has ? B.ws[lane].sum_out : 0u);
       if (lane == 4 && s_out) atomicAdd(&rs->sum_out, (unsigned long long)s_out);
     }
+    {
+      const uint32_t md = __reduce_max_sync(FULL, has ? B.ws[lane].max_din : 0u);
+      if (lane == 8 && md) atomicMax(&rs->max_din, md);
+    }
     if ((MODES & M_SCHED) && (D.flags & F_NEED_FEATURES)) {
       const uint32_t s_in = __reduce_add_sync(FULL, has ? B.ws[lane].sum_in : 0u);
       uint32_t h[3];
@@ -360,6 +370,7 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
     w.nlog = w.nw4 = w.nedge = w.nlive = w.ncount = 0;
     w.sum_in = w.sum_out = 0;
     w.hist[0] = w.hist[1] = w.hist[2] = 0;
+    w.max_din = 0;
   }
 }
 
@@ -564,6 +575,7 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
   const uint32_t len = ld_relaxed(&C->log_len);
   const unsigned long long w4 = ld_relaxed64(&C->w4);
   const uint32_t live_count = ld_relaxed(&rs->live_count);
+  const uint32_t max_din = ld_relaxed(&rs->max_din);
   unsigned long long sum_in = 0, sum_out = 0, t_r = 0, t_rm1 = 0;
   uint32_t h0 = 0, h1 = 0, h2 = 0;
   const bool live_edges = feats || (D.flags & F_LIVE_EDGES);
@@ -600,12 +612,14 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
     if (L.variant == TRIM_AC4_PUSH) {  // pushed every work-list entry that existed before round r
       L.c4w = L.w_end;
       L.e_c4 = L.e_end;
+      L.bmax = 0;
     }
     if (L.variant == TRIM_AC3_PULL) {
       L.ac3_list = L.live_out;
       L.live_in_len = live_count;
     }
   }
+  L.bmax = max(L.bmax, max_din);  // the entries of F_r join the AC-4 backlog
   if (cta0) {
     D.roff[r] = L.fe;
     D.roff[r + 1] = len;
@@ -690,6 +704,7 @@ __device__ __forceinline__ void start_round(const Dev& D, uint32_t k) {
     z->sum_in = 0; z->sum_out = 0;
     z->hist[0] = z->hist[1] = z->hist[2] = 0;
     z->live_count = 0;
+    z->max_din = 0;
   }
 }
 
@@ -711,6 +726,30 @@ __device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_
   const bool check = (MODES != M_AC4) && S.mixed;
   const uint32_t ea = S.e_c4, eb = S.e_end, ia = S.c4w, ib = S.w_end;
   if (eb <= ea) return;
+  // A small round (at most one entry and one 32-edge chunk per warp) whose
+  // entries all have few in-edges gives each warp one work-list entry: its row
+  // and edge range come with one load, no chunk-owner lookup, and the warp
+  // walks the entry's in-edges 32 at a time (at most 8 steps).
+  if (ib - ia <= nwarps && eb - ea <= 32u * nwarps && S.bmax <= 256u) {
+    const uint32_t j = ia + gwarp;
+    if (j < ib) {
+      const uint32_t row = ldcg(&D.w4_row[j]);
+      const uint32_t eo = ldcg(&D.w4_eoff[j]);
+      const uint32_t ee = (j + 1u < ib) ? ldcg(&D.w4_eoff[j + 1u]) : eb;
+      for (uint32_t k0 = eo; k0 < ee; k0 += 32u) {
+        const uint32_t e = k0 + lane;
+        const bool valid = e < ee;
+        const uint32_t u = valid ? __ldg(&D.itgt[row + (e - eo)]) : 0u;
+        const uint32_t old = valid ? atomicSub(&D.cnt[u], 1u) : 0u;
+        K.pushed += valid ? 1 : 0;
+        bool pred = valid && old == 1u;
+        if (pred && check) pred = ldcg(&D.level[u]) == LIVE;
+        append_dead(D, B, pred, u, r, D.live0);
+      }
+    }
+    stats_flush(D, K);
+    return;
+  }
   const uint32_t c0 = ea >> 5, c1 = (eb + 31u) >> 5;
   const uint32_t per = (c1 - c0 + nwarps - 1) / nwarps;
   const uint32_t cb = c0 + gwarp * per, ce = min(c1, cb + per);
@@ -1050,6 +1089,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     S.done = 0; S.fprev = 0; S.mixed = 0;
     S.vcount[0] = S.vcount[1] = S.vcount[2] = 0;
     S.stable = 0;
+    S.bmax = 0;
     S.m_live = D.m;
     for (int i = 0; i < NFEAT; ++i) S.feat[i] = 0.0f;
 
@@ -1057,6 +1097,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
       WarpSlice& x = B.ws[w];
       x.nlog = x.nw4 = x.nedge = x.nlive = x.ncount = 0;
       x.sum_in = x.sum_out = 0;
+      x.max_din = 0;
       x.hist[0] = x.hist[1] = x.hist[2] = 0;
     }
     B.epoch = 0;
