@@ -71,7 +71,7 @@ constexpr int WBUF = 64;        // per-warp staging of supporting-set members
 // Work counters (TRIM_FLAG_STATS). Each round function keeps its own in
 // registers and adds them to the global totals when it returns.
 struct Counters {
-  unsigned long long edges = 0, pushed = 0, cand = 0, swept = 0;
+  unsigned edges = 0, pushed = 0, cand = 0, swept = 0;  // one round: each at most m < 2^32
 };
 
 // Per-warp append slices. Each warp buffers what it removes (and, in AC-3
@@ -100,6 +100,7 @@ struct Cta {
   unsigned bar_base;  // barrier counter when this kernel started
   unsigned err;
   unsigned w4_wide;   // initial pass: the work-list slices take all four buffers
+  unsigned long long kstat[4];  // TRIM_FLAG_STATS totals of this CTA (see stats_flush)
   uint32_t wbuf[MAX_WARPS][WBUF];
 };
 
@@ -404,16 +405,26 @@ __device__ bool grid_barrier(const Dev& D, Cta& B, bool read_err = true) {
 }
 
 // Warp-collective: adds this warp's counters to the run totals (stats runs only).
-__device__ __forceinline__ void stats_flush(const Dev& D, const Counters& K) {
+// The CTA's totals stay in shared memory for the whole launch and reach the
+// global counters once, when the kernel ends (stats_publish): no global
+// atomics per warp and round.
+__device__ __forceinline__ void stats_flush(const Dev& D, Cta& B, const Counters& K) {
   if (!(D.flags & F_STATS)) return;
-  const unsigned long long e = warp_sum(K.edges), p = warp_sum(K.pushed), c = warp_sum(K.cand),
-                           s = warp_sum(K.swept);
+  // a round's counts of a whole warp are counts of distinct edges or vertices
+  const unsigned e = __reduce_add_sync(FULL, K.edges), p = __reduce_add_sync(FULL, K.pushed),
+                 c = __reduce_add_sync(FULL, K.cand), s = __reduce_add_sync(FULL, K.swept);
   if (lane_id() == 0) {
-    if (e) atomicAdd(&D.C->stats[0], e);
-    if (p) atomicAdd(&D.C->stats[1], p);
-    if (c) atomicAdd(&D.C->stats[2], c);
-    if (s) atomicAdd(&D.C->stats[3], s);
+    if (e) atomicAdd(&B.kstat[0], (unsigned long long)e);
+    if (p) atomicAdd(&B.kstat[1], (unsigned long long)p);
+    if (c) atomicAdd(&B.kstat[2], (unsigned long long)c);
+    if (s) atomicAdd(&B.kstat[3], (unsigned long long)s);
   }
+}
+
+__device__ __forceinline__ void stats_publish(const Dev& D, Cta& B) {
+  if (!(D.flags & F_STATS)) return;
+  __syncthreads();
+  if (threadIdx.x < 4 && B.kstat[threadIdx.x]) atomicAdd(&D.C->stats[threadIdx.x], B.kstat[threadIdx.x]);
 }
 
 // ------------------------------------------------------------------ scans
@@ -747,7 +758,7 @@ __device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_
         append_dead(D, B, pred, u, r, D.live0);
       }
     }
-    stats_flush(D, K);
+    stats_flush(D, B, K);
     return;
   }
   const uint32_t c0 = ea >> 5, c1 = (eb + 31u) >> 5;
@@ -785,7 +796,7 @@ __device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_
       append_dead(D, B, pred, u[q], r, D.live0);
     }
   }
-  stats_flush(D, K);
+  stats_flush(D, B, K);
 }
 
 // ------------------------------------------------------------------ AC-3
@@ -820,7 +831,7 @@ __device__ ROUND_FN void ac3_round(const Dev& D, Cta& B, const Sched& S, uint32_
     append_dead(D, B, dies, v, r, Lout, false, false, 0, 0, d);
     append_live(D, B, stays, v, r, Lout);
   }
-  stats_flush(D, K);
+  stats_flush(D, B, K);
 }
 
 // ------------------------------------------------------------------ AC-6
@@ -920,7 +931,7 @@ __device__ ROUND_FN bool ac6_entry(const Dev& D, Cta& B, const Sched& S, uint32_
     K.swept += has ? 1 : 0;
     append_dead(D, B, dies, v, r, D.live0, false, false, 0, 0, d);
   }
-  stats_flush(D, K);
+  stats_flush(D, B, K);
   if (!grid_barrier(D, B)) return false;
   // grid-wide exclusive scan of s_cnt into s_off
   const uint32_t chunk = ((n + gridDim.x - 1) / gridDim.x + 31) & ~31u;
@@ -1027,7 +1038,7 @@ __device__ ROUND_FN bool ac6_round(const Dev& D, Cta& B, const Sched& S, uint32_
       }
     }
   }
-  stats_flush(D, K);
+  stats_flush(D, B, K);
   return true;
 }
 
@@ -1103,6 +1114,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     B.epoch = 0;
     B.err = 0;
     B.w4_wide = 0;
+    B.kstat[0] = B.kstat[1] = B.kstat[2] = B.kstat[3] = 0;
   }
 #if TRIM_MODES & 8
   // blob layout W1[32][12] b1 W2[32][32] b2 W3[3][32] b3 mean istd lo hi; W1 and
@@ -1180,6 +1192,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     if (stamp) D.C->t_flush[S.round & 3] = globaltimer();
     ok = grid_barrier(D, B, false);
   }
+  stats_publish(D, B);  // every exit of the loop is taken by the whole CTA
 }
 
 // ---------------------------------------------------------------- helpers

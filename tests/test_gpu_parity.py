@@ -462,3 +462,30 @@ def test_launch_shapes_give_identical_results(block, cps):
         t.set_params(block_threads=block, ctas_per_sm=cps)
         for v in VARIANTS:
             check(t, lvl, st, alpha, f"{v}-{block}x{cps}", t.run(v))
+
+
+@pytest.mark.parametrize("i", [1, 2])
+def test_stats_count_every_pushed_in_edge(i):
+    """TRIM_FLAG_STATS: AC-4 pushes the in-edges of every removed vertex exactly
+    once, so in_edges_pushed is the in-degree sum of the removed vertices (from
+    the oracle's levels and G^T), for a single launch and for a scheduled run
+    split into segments alike."""
+    P = _P()
+    g = cfg.config_small(i)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    oi, ti = oracle.transpose(g.off, g.tgt)
+    din = np.diff(oi.astype(np.int64))
+    want = int(din[st == 0].sum())
+    with P.Trimmer(g.off, g.tgt, oi, ti, flags=P.TRIM_FLAG_STATS) as t:
+        s = t.run("ac4")
+        check(t, lvl, st, alpha, "ac4-stats", s)
+        assert s["in_edges_pushed"] == want
+        t.set_params(sched_commit_rounds=4, sched_recheck_rounds=16)
+        s = t.run("heuristic")
+        check(t, lvl, st, alpha, "heuristic-stats", s)
+        if s["rounds_by_variant"] == [alpha, 0, 0]:
+            assert s["in_edges_pushed"] == want, (s, want)
+        s = t.run("ac6")
+        assert s["in_edges_pushed"] == 0 and s["candidates"] > 0
+        s = t.run("ac3")
+        assert s["live_swept"] > 0
