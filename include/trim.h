@@ -14,7 +14,8 @@
  *    chunk arithmetic cannot wrap); 0xFFFFFFFF is the LIVE sentinel of
  *    trim_level.
  *  - Device pointers passed in are BORROWED: they must stay valid and unchanged
- *    until trim_destroy(). Host pointers are copied during the call.
+ *    until trim_destroy(); so are host arrays given as TRIM_MEM_HOST_MAPPED.
+ *    Other host pointers are copied during the call.
  *  - A context is bound to one CUDA stream and to the device current at
  *    trim_create(); it is not thread-safe. All device work is ordered on that
  *    stream.
