@@ -274,3 +274,52 @@ def test_ac6_inspects_each_edge_at_most_once():
         g = cfg.config_small(i)
         _, _, _, sc = oracle.ac6(g.off, g.tgt)
         assert sc <= g.m
+
+
+def test_transpose_is_the_reversed_edge_multiset():
+    """oracle.transpose: G^T holds every edge (u, v) of G as (v, u), with its
+    multiplicity, and its offsets are the prefix sums of the in-degrees; checked
+    against a dictionary of reversed edges built here, on graphs with duplicate
+    edges, self-loops, isolated vertices and unsorted rows."""
+    from collections import Counter
+    rng = np.random.default_rng(31)
+    for trial in range(20):
+        n = int(rng.integers(1, 60))
+        m = int(rng.integers(0, 5 * n))
+        src = np.sort(rng.integers(0, n, m))
+        dst = rng.integers(0, n, m)
+        off = np.zeros(n + 1, np.uint32)
+        np.add.at(off, src + 1, 1)
+        off = np.cumsum(off).astype(np.uint32)
+        tgt = dst.astype(np.uint32)
+        oi, ti = oracle.transpose(off, tgt)
+        assert oi[0] == 0 and int(oi[-1]) == m
+        indeg = Counter(int(d) for d in dst)
+        for v in range(n):
+            assert int(oi[v + 1] - oi[v]) == indeg.get(v, 0)
+        got = Counter((v, int(u)) for v in range(n) for u in ti[oi[v]:oi[v + 1]])
+        want = Counter((int(d), int(s)) for s, d in zip(src, dst))
+        assert got == want
+
+
+def test_forms_agree_with_brute_force_on_random_multigraphs():
+    """Property, many seeds: the three oracle forms (Alg. 5 peeling, Alg. 7
+    AC-6, Alg. 4 AC-3) and walk-length brute force give the same levels on
+    random multigraphs with self-loops, for densities from sparse to dense."""
+    rng = np.random.default_rng(47)
+    for trial in range(150):
+        n = int(rng.integers(1, 14))
+        dens = float(rng.uniform(0.0, 0.6))
+        adj = rng.random((n, n)) < dens
+        want = brute_levels(adj)
+        rows = []
+        for v in range(n):
+            r = [int(t) for t in np.nonzero(adj[v])[0]]
+            rng.shuffle(r)
+            if r and rng.random() < 0.5:
+                r = r + r[: int(rng.integers(1, len(r) + 1))]  # duplicates
+            rows.append(r)
+        g = gg.edges_from_lists(n, rows)
+        for lvl, st, alpha in run_all(g.off, g.tgt):
+            np.testing.assert_array_equal(lvl, want)
+            assert alpha == (int(want[want != LIVE].max()) + 1 if (want != LIVE).any() else 0)
