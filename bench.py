@@ -1,16 +1,21 @@
 """Benchmark: trimming throughput (edges/s = m / trim time) on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config I] [--variant V] [--sweep]
+                    [--config I] [--variant V] [--no-sweep] [--no-extra]
 
 A step is one complete trimming (every round, from the initial sink pass to the
-empty frontier) of the R-MAT scale-22 workload (configs index 1: 4,194,304
-vertices, edge factor 16, 10% sinks) with inputs resident in HBM; the L2 cache
-is flushed before every step and the step is timed with CUDA events on the
-library's stream. Rank 0 prints one JSON line.
+empty frontier) of the large mixed workload (configs index 4: R-MAT scale 26
+union a 2^25-vertex planted block with ~10,000-deep chains; n = 100.7M,
+m = 1.22e9, alpha = 10,004) with inputs resident in HBM, run with the learned
+per-round scheduler; the fixed variants and the heuristic are timed beside it
+on the same graph, and the R-MAT scale-22 workload (index 1) and the batched
+workload (index 3, one replayed CUDA graph against each graph trimmed alone)
+ride along as extra keys. The L2 cache is flushed before every step and the
+step is timed with CUDA events on the library's stream. Rank 0 prints one
+JSON line.
 
 --impl reference times the CPU oracle (sequential queue peeling, Algorithm 5
-run one step at a time) on the host on the same workload.
+run one step at a time) on the host on the same full workload graph.
 N > 1: independent replicas, one per GPU (trimming one graph has no sharded
 form here; see the design notes), value = edges of all ranks / max time.
 """
@@ -57,14 +62,9 @@ def workload(idx: int, small: bool = False):
 
 
 def host_transpose(off: np.ndarray, tgt: np.ndarray):
-    """G^T as plain data preparation (stable counting sort by target)."""
-    n = off.shape[0] - 1
-    src = np.repeat(np.arange(n, dtype=np.uint32), np.diff(off.astype(np.int64)))
-    order = np.argsort(tgt, kind="stable")
-    tgt_in = src[order]
-    off_in = np.zeros(n + 1, np.int64)
-    np.cumsum(np.bincount(tgt, minlength=n), out=off_in[1:])
-    return off_in.astype(np.uint32), tgt_in.astype(np.uint32)
+    """G^T as plain data preparation (the workloads supply both CSRs)."""
+    import graphgen
+    return graphgen.transpose(off, tgt)
 
 
 # ---------------------------------------------------------------- clocks
@@ -176,23 +176,41 @@ def kernel_source_sha() -> str:
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
-def profiled_traffic(config: int, small: bool, schedule: str):
-    """DRAM bytes per launch of the persistent kernel from the committed ncu
-    summary, if it covers this run (the rmat22 workload, AC-4) and was taken on
-    the current kernel source; else None."""
-    if config != 1 or small or schedule != "ac4" or not os.path.exists(PROFILE_TRAFFIC):
-        return None
+def _profile_fields(path: str) -> dict:
     kv = {}
-    for line in open(PROFILE_TRAFFIC):
+    for line in open(path, encoding="utf-8"):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
-            kv[k.strip()] = v.strip()
-    if kv.get("kernel_source_sha") != kernel_source_sha():
+            kv[k.strip()] = v.strip().split()[0] if v.strip() else ""
+    return kv
+
+
+def profiled_traffic(config: int, small: bool, schedule: str):
+    """DRAM bytes per run of the persistent kernel(s) from a committed ncu
+    summary under profiles/ that covers this workload (workload_config, small)
+    and schedule and was taken on the current kernel source; else None. The
+    summary of the R-MAT scale-22 AC-4 run predates the workload keys and
+    covers (1, full size, ac4)."""
+    sha = kernel_source_sha()
+    pdir = os.path.dirname(PROFILE_TRAFFIC)
+    if not os.path.isdir(pdir):
         return None
-    try:
-        return int(float(kv["dram_bytes_per_launch"]))
-    except (KeyError, ValueError):
-        return None
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith(".txt"):
+            continue
+        path = os.path.join(pdir, name)
+        kv = _profile_fields(path)
+        if path == PROFILE_TRAFFIC and "workload_config" not in kv:
+            kv.update(workload_config="1", small="0", schedule="ac4")
+        if kv.get("workload_config") != str(config) or kv.get("small", "0") != str(int(small)) \
+                or kv.get("schedule") != schedule or kv.get("kernel_source_sha") != sha:
+            continue
+        for key in ("dram_bytes_per_run", "dram_bytes_per_launch"):
+            try:
+                return int(float(kv[key]))
+            except (KeyError, ValueError):
+                pass
+    return None
 
 
 # ---------------------------------------------------------------- distributed
@@ -243,21 +261,21 @@ def sum_over_ranks(x: float, ws: int) -> float:
 
 # ---------------------------------------------------------------- CPU baseline
 
-def cpu_baseline(g, seconds: float = 12.0) -> dict:
-    """The oracle (sequential C, one thread) on the same graph, G^T prepared
-    outside the timing, repeated for about `seconds`."""
+def cpu_baseline(g, csr_in, seconds: float = 12.0) -> dict:
+    """The oracle (sequential C, one thread) on the same graph, G^T given as
+    input (prepared outside the timing, as for the GPU), repeated for about
+    `seconds` (at least 3 runs)."""
     import oracle
-    oi, ti = oracle.transpose(g.off, g.tgt)
     times = []
     t_end = time.perf_counter() + seconds
     while time.perf_counter() < t_end or len(times) < 3:
         t0 = time.perf_counter()
-        oracle.peel(g.off, g.tgt, (oi, ti))
+        oracle.peel(g.off, g.tgt, csr_in)
         times.append(time.perf_counter() - t0)
     mean = statistics.mean(times)
     return {"value": g.m / mean, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"the full workload graph, {len(times)} repeats of the single-threaded "
-                      f"oracle peel (G^T prepared once outside the timing), mean {mean * 1e3:.1f} ms",
+            "sample": f"the full workload graph, {len(times)} runs of the single-threaded "
+                      f"oracle peel (G^T given as input), mean {mean * 1e3:.1f} ms",
             "cpu": cpu_name(), "nproc": os.cpu_count()}
 
 
@@ -272,34 +290,43 @@ def cpu_name() -> str:
     return platform.machine()
 
 
+def reference_steps(t_one: float, steps: int, warmup: int, budget: float):
+    """(warm-up runs, timed runs) of the reference arm: the requested ones when
+    they fit the wall-clock budget, else as many as fit (the first, untimed
+    run counts as one warm-up; at least one timed run)."""
+    if t_one * (steps + max(0, warmup - 1)) <= budget:
+        return max(0, warmup - 1), steps
+    fit = max(1, int(budget / max(t_one, 1e-9)))
+    return 0, min(steps, fit)
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return
     import oracle
     g, wname = workload(args.config, args.small)
-    oi, ti = oracle.transpose(g.off, g.tgt)
-    # each step is one oracle run over the workload graph; when the requested
-    # steps would take longer than REFERENCE_BUDGET_S, each step is a run over
-    # the small graph of the same recipe instead (stated in the sample)
+    csr_in = host_transpose(g.off, g.tgt)
+    # every step is one oracle run over the full workload graph; when the
+    # requested steps would take longer than REFERENCE_BUDGET_S, fewer steps are
+    # timed (stated in the sample), never a different graph
     t0 = time.perf_counter()
-    oracle.peel(g.off, g.tgt, (oi, ti))
+    oracle.peel(g.off, g.tgt, csr_in)
     t_one = time.perf_counter() - t0
-    sample = f"the full workload graph per step, {args.steps} steps"
-    if t_one * (args.steps + args.warmup) > REFERENCE_BUDGET_S and not args.small:
-        import graphgen.configs as cfg
-        g = cfg.config_small(args.config)
-        oi, ti = oracle.transpose(g.off, g.tgt)
-        sample = (f"per step one run over the small graph of the same recipe ({g.name}, "
-                  f"m={g.m}): the full graph takes {t_one:.1f} s per run")
-    for _ in range(args.warmup):
-        oracle.peel(g.off, g.tgt, (oi, ti))
+    n_warm, n_steps = reference_steps(t_one, args.steps, args.warmup, REFERENCE_BUDGET_S)
+    for _ in range(n_warm):
+        oracle.peel(g.off, g.tgt, csr_in)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.peel(g.off, g.tgt, (oi, ti))
+    for _ in range(n_steps):
+        oracle.peel(g.off, g.tgt, csr_in)
     dt = time.perf_counter() - t0
-    value = g.m * args.steps / dt
+    value = g.m * n_steps / dt
+    sample = f"the full workload graph per step, {n_steps} timed steps after {n_warm + 1} untimed"
+    if n_steps < args.steps:
+        sample += (f" ({args.steps} requested: one run takes {t_one:.1f} s, the timed steps are "
+                   f"capped at {REFERENCE_BUDGET_S:.0f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "steps": n_steps, "warmup": n_warm + 1, "requested_steps": args.steps,
+            "ms_per_step": dt / n_steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": {"workload": wname, "n": g.n, "m": g.m},
@@ -312,13 +339,17 @@ def run_reference(args, rank, ws):
 
 # ---------------------------------------------------------------- GPU arm
 
-def apply_tuned(t, args, variant):
+def tuned_key(config: int, small: bool) -> str:
+    return f"config{config}{'-small' if small else ''}"
+
+
+def apply_tuned(t, args, variant, key=None):
     """Autotuned trim_params_t of this workload and variant (the autotuner's
     result file), unless --no-tuned or none were tuned; returns them."""
     if args.no_tuned:
         return {}
     from paper_2107_12720_gb300 import autotune
-    return autotune.apply(t, f"config{args.config}{'-small' if args.small else ''}", variant)
+    return autotune.apply(t, key or tuned_key(args.config, args.small), variant)
 
 
 def restore_defaults(t):
@@ -364,6 +395,41 @@ def time_variant(P, t, variant, steps, warmup, flush_buf, graph_off=None):
     return times, kern, last
 
 
+def sweep_variants(P, t, g, args, key, names, flush, gofs=None, label=""):
+    """Times every schedule in `names` on the context `t` (tuned parameters of
+    `key` applied per schedule, library defaults restored afterwards)."""
+    out = {}
+    for v in names:
+        tuned_v = apply_tuned(t, args, v, key)
+        ts, ks, st = time_variant(P, t, v, max(args.sweep_steps, args.steps // 10), 1, flush,
+                                  gofs)
+        restore_defaults(t)
+        out[v] = {"ms": statistics.mean(ts), "kernel_ms": statistics.mean(ks),
+                  "ms_ci95": (1.96 * statistics.stdev(ts) / len(ts) ** 0.5)
+                  if len(ts) > 1 else None,
+                  "params": tuned_v or "defaults",
+                  "edges_per_s": g.m / (statistics.mean(ts) * 1e-3),
+                  "rounds_by_variant": st["rounds_by_variant"], "segments": st["segments"]}
+        print(f"# {label}{v:10s} {statistics.mean(ts):8.4f} ms  kernel {statistics.mean(ks):8.4f} ms"
+              f"  {g.m / statistics.mean(ts) / 1e-3:.3e} edges/s  rounds {st['rounds_by_variant']}"
+              f"  segments {st['segments']}", file=sys.stderr, flush=True)
+    return out
+
+
+def schedules_summary(sweep: dict) -> dict:
+    """Best fixed variant of a sweep and every schedule's speed relative to it
+    (> 1: faster than the best fixed variant)."""
+    fixed = {v: sweep[v]["ms"] for v in ("ac4", "ac6", "ac3") if v in sweep}
+    if not fixed:
+        return {}
+    best = min(fixed, key=fixed.get)
+    out = {"best_fixed": best, "best_fixed_ms": fixed[best]}
+    for v in ("heuristic", "learned"):
+        if v in sweep:
+            out[f"{v}_vs_best_fixed"] = fixed[best] / sweep[v]["ms"]
+    return out
+
+
 def per_graph_fixed(P, g, variant="ac4", limit=None):
     """The unbatched schedule: every packed graph trimmed alone with one fixed
     variant (one context per graph, G^T given); returns the summed device time
@@ -384,7 +450,16 @@ def per_graph_fixed(P, g, variant="ac4", limit=None):
     return total_ms * scale, count
 
 
-def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None, mapped=True, params=None):
+def touched_input_bytes(n: int, st: dict) -> int:
+    """Bytes of distinct CSR entries the kernels read from host memory in place
+    (TRIM_MEM_HOST_MAPPED), from the run's work counters: the initial pass reads
+    both offset arrays whole; AC-4 reads the G^T row of every pushed in-edge;
+    AC-6/AC-3 read the target of every out-edge they inspect."""
+    return 8 * (n + 1) + 4 * int(st["in_edges_pushed"]) + 4 * int(st["edges_inspected"])
+
+
+def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None, mapped=True, params=None,
+                model=None):
     """Through the C ABI with host buffers, host wall clock around the whole
     call sequence: trim_create on page-locked host CSR (and G^T), trim_run,
     trim_level into a host array, trim_destroy. mapped: the kernels read the
@@ -401,13 +476,49 @@ def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None, mapped=Tru
         with P.Trimmer(ho, ht, hoi, hti, host_mapped=mapped) as t:
             if params:
                 t.set_params(**params)
+            if model is not None:
+                t.set_model(model)
             t.batch_run(graph_off, variant) if graph_off is not None else t.run(variant)
             P.trim_level(t.ctx, out.data_ptr(), 0)
         t1 = time.perf_counter()
         if s:  # the first call pays one-time costs (module load, context)
             ts.append(t1 - t0)
-    h2d = (g.off.nbytes + g.tgt.nbytes + off_in.nbytes + tgt_in.nbytes)
-    return g.m / statistics.mean(ts), h2d, out.numel() * 4
+    copied = (g.off.nbytes + g.tgt.nbytes + off_in.nbytes + tgt_in.nbytes)
+    del ho, ht, hoi, hti
+    return g.m / statistics.mean(ts), copied, out.numel() * 4
+
+
+def extra_workload(P, idx, args, flush, stream, model):
+    """A second workload timed in the same run (all its schedules; for the
+    batched workload also each graph trimmed alone), as a sub-object of the
+    JSON line."""
+    import torch
+    g, wname = workload(idx)
+    oi, ti = host_transpose(g.off, g.tgt)
+    dev = lambda a: torch.from_numpy(a.view(np.int32)).cuda()
+    bufs = [dev(g.off), dev(g.tgt), dev(oi), dev(ti)]
+    batched = idx == 3
+    gofs = g.graph_off if batched else None
+    names = ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if model is not None else [])
+    with P.Trimmer(*bufs, stream=stream) as t:
+        if model is not None:
+            t.set_model(model)
+        sweep = sweep_variants(P, t, g, args, tuned_key(idx, False), names, flush, gofs,
+                               label=f"[{idx}] ")
+    out = {"workload": wname, "n": g.n, "m": g.m, "variants": sweep,
+           "schedules": schedules_summary(sweep)}
+    if batched:
+        out["graphs"] = int(len(g.graph_off) - 1)
+        out["timing"] = ("CUDA events around trim_batch_run: one replayed CUDA graph "
+                         "(control-block reset + persistent kernel) for all graphs")
+        ms, cnt = per_graph_fixed(P, g, "ac4", args.per_graph if args.per_graph > 0 else None)
+        best = min(sweep[v]["ms"] for v in ("ac4", "ac6", "ac3"))
+        out["per_graph_fixed"] = {"schedule": "ac4, each graph trimmed alone (one launch each)",
+                                  "ms": ms, "value": g.m / (ms * 1e-3), "unit": UNIT,
+                                  "graphs_timed": cnt, "batched_speedup": ms / best}
+    del bufs
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args, rank, ws, local):
@@ -423,38 +534,31 @@ def run_ours(args, rank, ws, local):
     # timed runs carry no instrumentation; one extra run of a context with
     # TRIM_FLAG_STATS afterwards supplies the work counters
     t = P.Trimmer(d_off, d_tgt, d_oi, d_ti, stream=stream)
-    model = os.path.join(ROOT, "paper_2107_12720_gb300", "models", "scheduler_mlp.npy")
-    have_model = os.path.exists(model)
-    if have_model:
-        t.set_model(np.load(model))
+    model_path = os.path.join(ROOT, "paper_2107_12720_gb300", "models", "scheduler_mlp.npy")
+    model = np.load(model_path) if os.path.exists(model_path) else None
+    if model is not None:
+        t.set_model(model)
     # the plain variants are the measured schedules of the single-graph
     # workloads; the large mixed graph runs the learned scheduler
-    headline = args.variant or ("learned" if (args.config == 4 and have_model) else "ac4")
+    headline = args.variant or ("learned" if (args.config == 4 and model is not None) else "ac4")
     # the batched workload is a packed set of independent graphs; the large
     # mixed graph is also a union of parts, but one graph to trim
     batched = g.graph_off is not None and args.config == 3
     gofs = g.graph_off if batched else None
+    key = tuned_key(args.config, args.small)
 
     sweep = {}
     if args.sweep and rank == 0:
-        names = args.sweep_variants.split(",") if args.sweep_variants else \
-            ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if have_model else [])
-        for v in names:
-            tuned_v = apply_tuned(t, args, v)
-            ts, ks, st = time_variant(P, t, v, max(args.sweep_steps, args.steps // 10), 1, flush,
-                                      gofs)
-            restore_defaults(t)
-            sweep[v] = {"ms": statistics.mean(ts), "kernel_ms": statistics.mean(ks),
-                        "ms_ci95": (1.96 * statistics.stdev(ts) / len(ts) ** 0.5)
-                        if len(ts) > 1 else None,
-                        "params": tuned_v or "defaults",
-                        "edges_per_s": g.m / (statistics.mean(ts) * 1e-3),
-                        "rounds_by_variant": st["rounds_by_variant"]}
-            print(f"# {v:10s} {statistics.mean(ts):8.4f} ms  kernel {statistics.mean(ks):8.4f} ms"
-                  f"  {g.m / statistics.mean(ts) / 1e-3:.3e} edges/s  rounds {st['rounds_by_variant']}",
-                  file=sys.stderr, flush=True)
+        if args.sweep_variants:
+            names = args.sweep_variants.split(",")
+        else:
+            # AC-3 sweeps the live set every round: on the 10,004-round large
+            # graph that is hours of work, so it is left out there
+            names = (["ac4", "ac6"] + ([] if args.config == 4 and not args.small else ["ac3"])
+                     + ["heuristic"] + (["learned"] if model is not None else []))
+        sweep = sweep_variants(P, t, g, args, key, names, flush, gofs)
 
-    tuned = apply_tuned(t, args, headline)
+    tuned = apply_tuned(t, args, headline, key)
     clocks = ClockSampler(local)
     if rank == 0:
         clocks.start()
@@ -472,32 +576,45 @@ def run_ours(args, rank, ws, local):
     value = edges_total / total_s
     kernel_ms = statistics.mean(ks)
 
+    counts = st
+    if rank == 0:
+        with P.Trimmer(d_off, d_tgt, d_oi, d_ti, stream=stream, flags=P.TRIM_FLAG_STATS) as tc:
+            if model is not None:
+                tc.set_model(model)
+            apply_tuned(tc, args, headline, key)
+            counts = tc.batch_run(gofs, headline) if batched else tc.run(headline)
+    rate, probed = None, 0
+    if rank == 0 and counts["in_edges_pushed"] and not args.no_atomic_probe:
+        rate, probed = atomic_ceiling(P, t, off_in, tgt_in, counts["in_edges_pushed"])
+    t.close()
+
     e2e = None
     if rank == 0 and args.e2e_steps > 0:
         full = None
         if tuned:
             from paper_2107_12720_gb300 import autotune
             full = {**autotune.default_params(), **tuned}
-        ev, h2d, d2h = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs, True, full)
-        evc, _, _ = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs, False, full)
-        e2e = {"value": ev * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        ev, copied, d2h = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs, True,
+                                      full, model)
+        evc, _, _ = e2e_measure(P, g, off_in, tgt_in, headline, args.e2e_steps, gofs, False,
+                                full, model)
+        e2e = {"value": ev * ws, "unit": UNIT,
+               "h2d_bytes_per_step": touched_input_bytes(g.n, counts),
                "d2h_bytes_per_step": d2h,
                "inputs": "page-locked host CSR + G^T read in place by the kernels "
-                         "(TRIM_MEM_HOST_MAPPED, NVLink-C2C); levels copied back to host",
+                         "(TRIM_MEM_HOST_MAPPED, NVLink-C2C); levels copied back to host. "
+                         "h2d_bytes_per_step: the distinct CSR entries the kernels read, from "
+                         "the work counters (both offset arrays, the G^T row of every pushed "
+                         "in-edge, the target of every inspected out-edge)",
+               "host_csr_bytes": copied,
                "copy_inputs_value": evc * ws,
-               "copy_inputs": "same calls with the CSR first copied to device memory "
-                              "(TRIM_MEM_HOST)"}
-    counts = st
-    if rank == 0:
-        with P.Trimmer(d_off, d_tgt, d_oi, d_ti, stream=stream, flags=P.TRIM_FLAG_STATS) as tc:
-            if have_model:
-                tc.set_model(np.load(model))
-            apply_tuned(tc, args, headline)
-            counts = tc.batch_run(gofs, headline) if batched else tc.run(headline)
-    rate, probed = None, 0
-    if rank == 0 and counts["in_edges_pushed"] and not args.no_atomic_probe:
-        rate, probed = atomic_ceiling(P, t, off_in, tgt_in, counts["in_edges_pushed"])
-    t.close()
+               "copy_inputs": f"same calls with the whole CSR + G^T ({copied} bytes) first "
+                              "copied to device memory (TRIM_MEM_HOST)"}
+
+    extra = {}
+    if rank == 0 and args.extra and args.config == 4 and not args.small:
+        for idx in (1, 3):
+            extra[f"config{idx}"] = extra_workload(P, idx, args, flush, stream, model)
     if rank != 0:
         return
     peak, peak_kind = measured_peaks()
@@ -512,16 +629,20 @@ def run_ours(args, rank, ws, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wname, "n": g.n, "m": g.m, "schedule": headline,
                    "rounds": st["rounds"], "rounds_by_variant": st["rounds_by_variant"],
+                   "segments": st["segments"],
                    "params": tuned or "library defaults",
                    "l2": "flushed before every step (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
-                   "timing": "CUDA events on the library stream around reset + persistent kernel"},
+                   "timing": "CUDA events on the library stream around reset + persistent "
+                             "kernel(s) (a scheduled run: all its segments)"},
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": st["launches"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(args.config, args.small, headline),
-                     "kernel": "trim_persistent_kernel", "kernel_ms": kernel_ms,
+                     "frac": achieved / peak,
+                     "traffic": profiled_traffic(args.config, args.small, headline),
+                     "kernel": "trim_persistent_kernel (all launches of one run)",
+                     "kernel_ms": kernel_ms,
                      "algorithmic_bytes": alg, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "l2_atomics": None if rate is None else {
@@ -533,13 +654,7 @@ def run_ours(args, rank, ws, local):
     }
     if sweep:
         line["variants"] = sweep
-        fixed = {v: sweep[v]["ms"] for v in ("ac4", "ac6", "ac3") if v in sweep}
-        if fixed:
-            best = min(fixed, key=fixed.get)
-            line["schedules"] = {"best_fixed": best, "best_fixed_ms": fixed[best]}
-            for v in ("heuristic", "learned"):
-                if v in sweep:
-                    line["schedules"][f"{v}_vs_best_fixed"] = fixed[best] / sweep[v]["ms"]
+        line["schedules"] = schedules_summary(sweep)
     if batched:
         line["config"]["graphs"] = int(len(g.graph_off) - 1)
         line["config"]["timing"] = ("CUDA events around trim_batch_run: one replayed CUDA graph "
@@ -550,18 +665,20 @@ def run_ours(args, rank, ws, local):
                                        "value": g.m / (ms * 1e-3), "unit": UNIT,
                                        "graphs_timed": cnt,
                                        "batched_speedup": ms / (step_s * 1e3)}
+    if extra:
+        line["other_workloads"] = extra
     if not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(g, (off_in, tgt_in), args.cpu_seconds)
     print(json.dumps(line), flush=True)
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--config", type=int, default=4)
     ap.add_argument("--variant", default=None)
     ap.add_argument("--small", action="store_true",
                     help="the small case of --config (parity-test size), for profiling")
@@ -569,16 +686,19 @@ def main(argv=None):
                     help="skip timing every variant next to the headline schedule")
     ap.add_argument("--sweep-variants", default="", help="comma-separated subset for --sweep")
     ap.add_argument("--sweep-steps", type=int, default=20)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="large mixed workload: skip timing the R-MAT scale-22 and batched "
+                         "workloads beside it")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tuned", action="store_true",
                     help="library default parameters instead of the autotuned ones")
     ap.add_argument("--no-atomic-probe", action="store_true",
                     help="skip measuring the L2 atomic ceiling of the run's pushes")
-    ap.add_argument("--per-graph", type=int, default=0,
-                    help="batched workload: also time each graph alone (N>0: a sample of N graphs, "
-                         "-1: all)")
+    ap.add_argument("--per-graph", type=int, default=256,
+                    help="batched workload: also time each graph alone (N>0: a sample of N graphs "
+                         "scaled to all, -1: all, 0: skip)")
     args = ap.parse_args(argv)
     rank, ws, local = dist_setup()
     if args.impl == "reference":

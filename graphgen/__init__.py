@@ -60,6 +60,8 @@ def _L():
             lib.gg_er.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, u32p, u32p]
             lib.gg_relabel.restype = None
             lib.gg_relabel.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u32p, u32p]
+            lib.gg_transpose.restype = ctypes.c_int
+            lib.gg_transpose.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u32p]
             lib.gg_word.restype = ctypes.c_uint64
             lib.gg_word.argtypes = [ctypes.c_uint64] * 3
             lib.gg_perm.restype = ctypes.c_uint32
@@ -181,6 +183,24 @@ def union(graphs, name="union") -> Graph:
         tgt[eo[i]:eo[i + 1]] = g.tgt + np.uint32(vo[i])
     off[-1] = np.uint32(eo[-1])
     return Graph(off, tgt, name, graph_off=vo.astype(np.uint32))
+
+
+def transpose(off, tgt):
+    """G^T of a CSR graph as (off_in, tgt_in), rows in ascending source order:
+    the in-CSR the workloads supply next to the out-CSR (input preparation,
+    parallel; the oracle keeps its own transpose)."""
+    off = np.ascontiguousarray(off, np.uint32)
+    tgt = np.ascontiguousarray(tgt, np.uint32)
+    n = off.shape[0] - 1
+    m = int(off[-1]) if n >= 0 else 0
+    off_in = np.empty(n + 1, np.uint32)
+    tgt_in = np.empty(max(m, 1), np.uint32)
+    rc = _L().gg_transpose(n, off, tgt if tgt.size else np.zeros(1, np.uint32), off_in, tgt_in)
+    if rc == -1:
+        raise ValueError("transpose: target out of range")
+    if rc != 0:
+        raise MemoryError("transpose: allocation failed")
+    return off_in, tgt_in[:m]
 
 
 def word(seed: int, stream: int, i: int) -> int:

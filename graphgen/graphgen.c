@@ -375,6 +375,57 @@ void gg_relabel(uint32_t n, const uint32_t* off, const uint32_t* tgt, const uint
   free(inv);
 }
 
+/* ---------- transposed graph (input preparation) ---------- */
+
+/* sorts row[0..len) ascending, keeping duplicates */
+static void sort_row(uint32_t* row, uint32_t len) {
+  if (len <= 32) {
+    for (uint32_t i = 1; i < len; ++i) {
+      uint32_t x = row[i]; int64_t j = (int64_t)i - 1;
+      while (j >= 0 && row[j] > x) { row[j + 1] = row[j]; --j; }
+      row[j + 1] = x;
+    }
+  } else {
+    qsort(row, len, sizeof(uint32_t), cmp_u32);
+  }
+}
+
+/* G^T of a CSR graph: off_in[v]..off_in[v+1] lists the sources of the edges into
+ * v, in ascending order (a parallel counting sort by target, then each row
+ * sorted, so the result does not depend on the thread count). Parallel edges
+ * appear once per copy. Returns 0, -1 if a target is >= n, -2 without memory. */
+int gg_transpose(uint32_t n, const uint32_t* off, const uint32_t* tgt, uint32_t* off_in,
+                 uint32_t* tgt_in) {
+  const uint64_t m = off[n];
+  uint32_t* fill = (uint32_t*)calloc((size_t)n + 1, sizeof(uint32_t));
+  if (!fill) return -2;
+  int bad = 0;
+  #pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int64_t e = 0; e < (int64_t)m; ++e) {
+    const uint32_t t = tgt[e];
+    if (t >= n) { bad = 1; continue; }
+    #pragma omp atomic
+    fill[t]++;
+  }
+  if (bad) { free(fill); return -1; }
+  uint64_t acc = 0;
+  for (uint32_t v = 0; v < n; ++v) { off_in[v] = (uint32_t)acc; acc += fill[v]; fill[v] = 0; }
+  off_in[n] = (uint32_t)acc;
+  #pragma omp parallel for schedule(dynamic, 4096)
+  for (int64_t u = 0; u < (int64_t)n; ++u)
+    for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+      const uint32_t t = tgt[e];
+      uint32_t slot;
+      #pragma omp atomic capture
+      slot = fill[t]++;
+      tgt_in[off_in[t] + slot] = (uint32_t)u;
+    }
+  #pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t v = 0; v < (int64_t)n; ++v) sort_row(tgt_in + off_in[v], off_in[v + 1] - off_in[v]);
+  free(fill);
+  return 0;
+}
+
 /* ---------- deterministic real helpers (no libm: identical on every host) ---------- */
 
 /* e^x by range reduction x = k ln2 + r, |r| <= ln2/2, and a degree-16 Taylor

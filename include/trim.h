@@ -300,7 +300,13 @@ trim_err_t trim_probe_atomic_rate(const uint32_t* idx, uint64_t n_idx, uint32_t*
  * context, or on its own), and level_out (n uint32: levels as trim_level,
  * TRIM_LIVE for survivors). rounds_out (host, nullable) receives alpha.
  * Sizes above TRIM_NOALLOC_MAX_N vertices or TRIM_NOALLOC_MAX_M edges are
- * rejected with TRIM_ERR_TOO_LARGE before any device work.
+ * rejected with TRIM_ERR_TOO_LARGE before any device work. The arrays
+ * themselves are not checked (as with trim_create without TRIM_FLAG_VALIDATE):
+ * offsets must be monotone with offsets[n] = m, every target < n, and
+ * (in_offsets, in_targets) exactly the transpose of (offsets, targets);
+ * otherwise the kernel may write outside level_out or the scratch array.
+ * cuda_stream must belong to the current device (NULL: its legacy default
+ * stream); a stream of another device is refused with TRIM_ERR_INVALID_ARG.
  *
  * The first call on each device (with that device current) looks up the
  * array's device address and the launch shape; make that first call before

@@ -733,8 +733,10 @@ __device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_
   Counters K;
   const unsigned lane = lane_id();
   const uint32_t r = S.round;
-  // a vertex whose counter reaches zero is still live unless another variant ran
-  const bool check = (MODES != M_AC4) && S.mixed;
+  // a vertex whose counter reaches zero is still live unless another variant
+  // ran (also in the AC-4-only flavour: a committed stretch of a scheduled run
+  // may follow AC-6 or AC-3 rounds, whose removals AC-4 has not yet pushed)
+  const bool check = S.mixed;
   const uint32_t ea = S.e_c4, eb = S.e_end, ia = S.c4w, ib = S.w_end;
   if (eb <= ea) return;
   // A small round (at most one entry and one 32-edge chunk per warp) whose

@@ -110,10 +110,18 @@ extern "C" trim_err_t trim_run_ac4_noalloc(const uint32_t* offsets, const uint32
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (!(major == 10 && minor == 3)) return TRIM_ERR_NO_DEVICE;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  // the scratch address and the launch shape belong to the current device: a
+  // stream of another device would receive pointers of the wrong context
+  int stream_dev = -1;
+  if (cudaStreamGetDevice(stream, &stream_dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TRIM_ERR_INVALID_ARG;
+  }
+  if (stream_dev != dev) return TRIM_ERR_INVALID_ARG;
   DeviceSetup* s = nullptr;
   trim_err_t e = setup_device(dev, &s);
   if (e != TRIM_OK) return e;
-  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   uint32_t* base = s->scratch;
 
   trimk::Dev D{};

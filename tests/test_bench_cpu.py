@@ -35,3 +35,31 @@ def test_traffic_only_for_the_profiled_run():
     assert bench.profiled_traffic(1, False, "learned") is None
     t = bench.profiled_traffic(1, False, "ac4")
     assert t is None or t > 0
+
+
+def test_reference_arm_keeps_the_graph_and_caps_the_steps():
+    # requested steps that fit the budget are all timed
+    assert bench.reference_steps(1.0, 20, 5, 150.0) == (4, 20)
+    # a slow graph: fewer timed steps, never zero, and no extra warm-up
+    assert bench.reference_steps(4.0, 20, 5, 150.0) == (4, 20)
+    assert bench.reference_steps(10.0, 20, 5, 150.0) == (0, 15)
+    assert bench.reference_steps(500.0, 20, 5, 150.0) == (0, 1)
+
+
+def test_touched_bytes_of_in_place_inputs():
+    st = {"in_edges_pushed": 100, "edges_inspected": 7}
+    assert bench.touched_input_bytes(10, st) == 8 * 11 + 4 * 100 + 4 * 7
+
+
+def test_input_transpose_equals_the_oracles():
+    """The G^T the workloads supply (graphgen, parallel) is the same array pair
+    as the oracle's own transpose, duplicates and empty rows included."""
+    import numpy as np
+    import graphgen as gg
+    import graphgen.configs as cfg
+    import oracle
+    graphs = [cfg.config_small(i) for i in range(4)]
+    graphs.append(gg.edges_from_lists(5, [[1, 1, 1], [2, 2], [], [3, 0, 0], [4]]))
+    for g in graphs:
+        a, b = gg.transpose(g.off, g.tgt), oracle.transpose(g.off, g.tgt)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), g

@@ -263,6 +263,47 @@ def test_committed_stretches_on_a_deep_cascade():
         assert s["segments"] == _commit_segments(alpha, K, P0), (s["segments"], alpha)
 
 
+def _first_round_ac6_model():
+    """A hand-set scheduler MLP (the TRIM_MLP_NBLOB layout) that picks AC-6 for
+    round 1 (its variant feature is -1 before any round) and AC-4 for every
+    later round: h1_0 = relu(-f11), h2_0 = h1_0, logits (1, 10 h2_0, -10)."""
+    import paper_2107_12720_gb300 as P
+    nin, nh = P.abi.TRIM_MLP_NIN, P.abi.TRIM_MLP_NH
+    W1 = np.zeros((nh, nin), np.float32); W1[0, 11] = -1.0
+    b1 = np.zeros(nh, np.float32)
+    W2 = np.zeros((nh, nh), np.float32); W2[0, 0] = 1.0
+    b2 = np.zeros(nh, np.float32)
+    W3 = np.zeros((3, nh), np.float32); W3[1, 0] = 10.0
+    b3 = np.array([1.0, 0.0, -10.0], np.float32)
+    norm = [np.zeros(nin, np.float32), np.ones(nin, np.float32),
+            np.full(nin, -1e30, np.float32), np.full(nin, 1e30, np.float32)]
+    blob = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3, *norm])
+    assert blob.size == P.abi.TRIM_MLP_NBLOB
+    return blob
+
+
+def test_commit_to_ac4_after_ac6_rounds():
+    """A learned run whose model picks AC-6 for round 1 and AC-4 afterwards,
+    committing after a single stable round: the run commits to AC-6 first, and
+    after the first stretch to AC-4 on the AC-4-only kernel, whose first round
+    pushes the backlog of every vertex AC-6 removed. Counters of vertices AC-6
+    already removed reach zero there; they must not be removed a second time."""
+    P = _P()
+    for i in [2, 0, 4]:
+        g = cfg.config_small(i)
+        lvl, st, alpha = oracle.peel(g.off, g.tgt)
+        off, tgt = dev_csr(g)
+        oi, ti = dev_csr_in(g)
+        with P.Trimmer(off, tgt, oi, ti, flags=P.TRIM_FLAG_ROUND_LOG) as t:
+            t.set_model(_first_round_ac6_model())
+            t.set_params(sched_commit_rounds=1, sched_recheck_rounds=4)
+            s = t.run("learned")
+            check(t, lvl, st, alpha, f"learned-ac6-then-ac4[{i}]", s)
+            v = [r.variant for r in t.round_log()]
+            assert v[0] == 1 and (alpha < 6 or v[-1] == 0), v[:8]
+            assert s["rounds_by_variant"][0] > 0 and s["rounds_by_variant"][1] > 0
+
+
 def _commit_segments(alpha, K, P0):
     """Launches of a scheduled run whose choice never changes: rounds 1..alpha;
     the choice has been kept for K rounds at the start of round K, where the run
@@ -413,16 +454,19 @@ def test_full_batched_workload():
 def test_full_large_mixed_workload_certificate():
     """The large mixed workload at full size (R-MAT scale 26 union a 2^25-vertex
     planted block: n = 100.7M, m = 1.22e9, alpha = 10,004) in the launch shape the
-    benchmark uses. Checked with the oracle's certificate, which holds for exactly
+    benchmark uses, with the fixed AC-4 variant and both schedulers (the learned
+    one is the benchmark's headline schedule on this graph). Checked with the oracle's certificate, which holds for exactly
     one status/level assignment (the trimming result), plus the planted block's
     closed form (C and R live, chain vertices at their chain position)."""
     P = _P()
+    from paper_2107_12720_gb300 import scheduler
     u = cfg.config(4)
     off, tgt = dev_csr(u)
     rmat_n = u.meta["rmat_n"]
     nC, nR, nT, chains = u.meta["block"]
     with P.Trimmer(off, tgt) as t:
-        for v in ["ac4", "heuristic"]:
+        t.set_model(scheduler.load_blob())
+        for v in ["ac4", "heuristic", "learned"]:
             s = t.run(v)
             lvl = t.level(device=False)
             st = t.status(device=False)

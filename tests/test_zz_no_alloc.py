@@ -39,13 +39,19 @@ def levels_with_allocating_entry_point(g):
         return t.level(device=False), stats["rounds"]
 
 
-def levels_without_allocation(g, d_off, d_tgt, d_ioff, d_itgt):
+def levels_without_allocation(g, d_off, d_tgt, d_ioff, d_itgt, tail=0):
+    """Levels from the entry point that allocates nothing. The output buffer is
+    poisoned (every level must be written) and, with tail > 0, has `tail` extra
+    poisoned entries after the n levels that must stay untouched."""
     import torch
     import paper_2107_12720_gb300 as P
-    out = torch.full((g.n,), -7, dtype=torch.int32, device="cuda")  # poison: all must be written
+    out = torch.full((g.n + tail,), -7, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     rounds = P.abi.trim_run_ac4_noalloc(d_off, d_tgt, d_ioff, d_itgt, g.n, g.m, out, stream)
-    return out.cpu().numpy().view(np.uint32), rounds
+    got = out.cpu().numpy().view(np.uint32)
+    if tail:
+        assert (got[g.n:] == np.uint32(0xFFFFFFF9)).all(), "wrote past level_out[n)"
+    return got[:g.n], rounds
 
 
 def test_no_alloc_entry_point_matches_trim_run_on_consecutive_calls():
@@ -61,6 +67,23 @@ def test_no_alloc_entry_point_matches_trim_run_on_consecutive_calls():
             bad = np.nonzero(got != want)[0]
             assert bad.size == 0, f"{g}: call {call}: {bad.size} levels differ"
             assert rounds == want_rounds
+
+
+def test_no_alloc_entry_point_at_its_size_limit():
+    """A graph with exactly the largest vertex count the scratch holds (2^18)
+    and close to the largest edge count (an R-MAT of scale 18 with edge factor
+    16: 2^22 draws before self-loops, duplicates and sinks are dropped), so that
+    every scratch region is used up to its end; level_out has a poisoned tail."""
+    g = gg.rmat(11, 18, 16, 0.57, 0.19, 0.19, 0.1, name="rmat18")
+    assert g.n == (1 << 18) and 0.8 * (1 << 22) < g.m <= (1 << 22)
+    want, want_rounds = levels_with_allocating_entry_point(g)
+    ioff, itgt = transpose_np(g.off, g.tgt)
+    dev = on_device(g.off, g.tgt, ioff, itgt)
+    for call in range(2):
+        got, rounds = levels_without_allocation(g, *dev, tail=64)
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, f"call {call}: {bad.size} levels differ"
+        assert rounds == want_rounds
 
 
 def test_no_alloc_entry_point_refuses_sizes_beyond_its_scratch():
