@@ -116,6 +116,13 @@ typedef struct {
                                  with TRIM_ERR_TIMEOUT                                       */
   float heur_push_ratio;      /* heuristic: push while sum(indeg F) < ratio * n_live        */
   float heur_ac6_ratio;       /* heuristic (no G^T): AC-6 while |F| < ratio * n_live        */
+  uint32_t local_round_edges; /* AC-4-only kernel: once the in-edges still to push fit a
+                                 small round (at most this many, one work-list entry per
+                                 warp), rounds run CTA-locally: each CTA queues the vertices
+                                 it removes in shared memory and pushes them itself in the
+                                 next round, and a round ends at one barrier that carries
+                                 its totals; a round whose removals overflow the queues
+                                 returns to ordinary rounds (0 = never local)            */
 } trim_params_t;
 
 /* Statistics of the last run (sizes in vertices/edges, times in ms). */
@@ -317,7 +324,7 @@ trim_err_t trim_probe_atomic_rate(const uint32_t* idx, uint64_t n_idx, uint32_t*
  * cuda_stream before it returns, to report device-side errors. */
 #define TRIM_NOALLOC_MAX_N (1u << 18)
 #define TRIM_NOALLOC_MAX_M (1u << 22)
-#define TRIM_NOALLOC_SCRATCH_BYTES 5769216u
+#define TRIM_NOALLOC_SCRATCH_BYTES 5769472u
 trim_err_t trim_run_ac4_noalloc(const uint32_t* offsets, const uint32_t* targets,
                                 const uint32_t* in_offsets, const uint32_t* in_targets,
                                 uint32_t n, uint32_t m, uint32_t* level_out,

@@ -41,7 +41,7 @@ class TrimParams(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("sched_commit_rounds", ctypes.c_uint32), ("sched_recheck_rounds", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("heur_push_ratio", ctypes.c_float),
-                ("heur_ac6_ratio", ctypes.c_float)]
+                ("heur_ac6_ratio", ctypes.c_float), ("local_round_edges", ctypes.c_uint32)]
 
 
 class TrimRunStats(ctypes.Structure):

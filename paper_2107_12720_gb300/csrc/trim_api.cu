@@ -230,6 +230,7 @@ void default_params(trim_params_t* p) {
   p->spin_limit_ns = 5ull * 1000 * 1000 * 1000;  // 5 s
   p->heur_push_ratio = 1.0f;
   p->heur_ac6_ratio = 1.0f;
+  p->local_round_edges = 1u << 20;
 }
 
 // per-warp append slices in dynamic shared memory: 4 buffers (dead log, AC-4
@@ -601,6 +602,7 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   D.heur_ac6_ratio = c->params.heur_ac6_ratio;
   D.commit_after = commit_after;
   D.stop_round = 0;
+  D.local_edges_max = c->params.local_round_edges;
   // segmented scheduled runs keep the live-edge count through lean stretches
   if (variant >= TRIM_SCHED_HEURISTIC && seg_flavour >= 0) D.flags |= trimk::F_LIVE_EDGES;
   // a fixed variant runs on its lean single-variant flavour
@@ -719,7 +721,7 @@ trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read) {
     }
     trim_run_stats_t s{};
     s.rounds = h.rounds;
-    s.n_dead = h.log_len;
+    s.n_dead = h.n_dead;
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     s.device_ms = ms;

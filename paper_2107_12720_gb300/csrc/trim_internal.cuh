@@ -63,6 +63,13 @@ struct Sched {
   uint32_t bmax;          // largest in-degree among work-list entries AC-4 has not pushed
   unsigned long long m_live;     // out-edges of live vertices
   float feat[12];                // features that chose this round's variant
+  // local AC-4 rounds (see trim_kernels.cu): removals counted only through the
+  // local barrier are not in Ctrl::log_len; `skew` holds them, so that
+  // removals so far = log_len + skew and logged entry i of the count sits at
+  // log position i - skew
+  uint32_t skew;
+  uint32_t lround;               // local rounds run so far (parity picks the barrier slot)
+  unsigned long long lbase[2];   // value of each local-barrier slot after its last round
 };
 
 // Global control block. Counters hit by every CTA sit on their own 128-byte lines.
@@ -81,6 +88,14 @@ struct Ctrl {
   unsigned long long t_flush[4];  // ... when CTA 0 finished flushing round r
   unsigned long long stats[4];    // edges inspected, in-edges pushed, candidates, live swept
   RoundStat rs[4];
+  // local AC-4 rounds: one 64-bit barrier word per round parity; every CTA adds
+  // 2^48 (arrival) + 2^32 (if it sent removals to the global lists) + its local
+  // removals, and reads the round's totals as the difference to the slot's
+  // value after its previous round
+  alignas(128) unsigned long long lbar[2];  unsigned int _p4[28];
+  unsigned long long local_edges; // in-edges pushed from the CTAs' local queues (live-edge count)
+  unsigned int n_dead;            // removals so far, published by CTA 0
+  unsigned int _p5[29];
   // segmented runs: a kernel that lacks the variant its scheduler picked saves
   // the schedule state here and exits; the kernel that has it resumes from it
   unsigned int resume;            // 1: a segment ended early, state in `saved`
@@ -120,6 +135,7 @@ struct Dev {
   uint32_t stop_round;    // != 0: hand the run back to the host at the start of this round
   uint32_t commit_after;  // != 0: scheduler flavours commit after this many stable rounds
   uint32_t bar_base;  // grid-barrier counter when this kernel starts (0 for a new run)
+  uint32_t local_edges_max;  // AC-4: pending in-edges up to which rounds run locally (0: never)
   Ctrl* C;
   trim_round_rec_t* rlog;
   uint32_t rlog_cap;
@@ -151,6 +167,14 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_relaxed_add64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");

@@ -89,6 +89,25 @@ struct WarpSlice {
   uint32_t max_din;          // largest in-degree among this warp's work-list entries
 };
 
+// Local AC-4 rounds (the AC-4-only flavour): while the pending work is small,
+// each CTA keeps the vertices it removes in a shared-memory queue together with
+// their predecessors (their G^T rows, loaded when they are removed) and
+// decrements those predecessors' counters itself in the next round. A round then
+// needs neither the dead log nor the work list in global memory, nor space
+// reservations, nor a read of the control block: it ends at a barrier that
+// carries the round's totals (see local_barrier). A removal that does not fit
+// the queue goes to the global lists, and the run returns to ordinary rounds.
+#if TRIM_MODES == 1
+#define TRIM_LOCAL 1
+#else
+#define TRIM_LOCAL 0
+#endif
+#if TRIM_LOCAL
+constexpr uint32_t LQ_EDGES = 1024;   // predecessors queued per CTA per round
+constexpr uint32_t LQ_ENTRIES = 256;  // removed vertices queued per CTA per round
+constexpr uint32_t LQ_DMAX = 64;      // larger in-degrees always go to the global work list
+#endif
+
 // Per-CTA shared state.
 struct Cta {
 #if TRIM_MODES & 8
@@ -102,6 +121,19 @@ struct Cta {
   unsigned w4_wide;   // initial pass: the work-list slices take all four buffers
   unsigned long long kstat[4];  // TRIM_FLAG_STATS totals of this CTA (see stats_flush)
   uint32_t wbuf[MAX_WARPS][WBUF];
+#if TRIM_LOCAL
+  // local queues, double-buffered by local-round parity: buffer b is filled in
+  // the round whose lround parity is b and read in the next one
+  uint32_t lq_ids[2][LQ_EDGES];       // predecessors to decrement
+  uint32_t lq_row[2][LQ_ENTRIES];     // the queued vertices' G^T rows ...
+  uint32_t lq_din[2][LQ_ENTRIES];     // ... and in-degrees
+  unsigned long long lq_cnt[2];       // reserved: entries (low 32) | predecessors (high 32)
+  uint32_t lq_vend[2];                // end of the reservations that fit (entries)
+  uint32_t lq_k;                      // this round's removals kept local
+  uint32_t lq_ovf;                    // 1: a removal of this round went to the global lists
+  uint32_t lq_pushed;                 // predecessors decremented from the queue this round
+  unsigned long long lq_delta;        // the round's totals from the local barrier
+#endif
 };
 
 // dynamic shared memory: per warp w, 4 slices of LW words at w * 4 * LW:
@@ -119,6 +151,19 @@ __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long l
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void red_relaxed_add(unsigned* p, unsigned v) {
   asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Warp-collective search: owner lane j of element k, i.e. the largest j with
+// excl_j <= k (lanes that own nothing carry excl = total and are never picked).
+__device__ __forceinline__ unsigned owner_of(unsigned excl, unsigned k) {
+  unsigned lo = 0;
+#pragma unroll
+  for (unsigned step = 16; step >= 1; step >>= 1) {
+    const unsigned cand = lo + step;
+    const unsigned ex = __shfl_sync(FULL, excl, cand & 31u);
+    if (cand < 32u && ex <= k) lo = cand;
+  }
+  return lo;
 }
 
 // ------------------------------------------------------------------ appends
@@ -302,6 +347,103 @@ __device__ __forceinline__ void append_live(const Dev& D, Cta& B, bool pred, uin
   __syncwarp();
 }
 
+#if TRIM_LOCAL
+// Warp-collective: lanes with pred add a work-list entry (G^T row start, in-degree)
+// of a vertex that is already removed and counted (local queue entries handed
+// to the global work list when local rounds end).
+__device__ __forceinline__ void append_w4(const Dev& D, Cta& B, bool pred, uint32_t row,
+                                          uint32_t din, uint32_t r) {
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const bool w = pred && din > 0u;
+  const unsigned wmask = __ballot_sync(FULL, w);
+  if (wmask == 0u) return;
+  const unsigned kw = __popc(wmask);
+  const unsigned ew = w ? din : 0u;
+  const unsigned eincl = warp_incl_scan(ew);
+  const unsigned esum = __shfl_sync(FULL, eincl, 31);
+  WarpSlice& ws = B.ws[warp];
+  if (ws.nw4 + kw > w4_cap(B)) warp_flush(D, B, r, D.live0);
+  const uint32_t pw = ws.nw4, pe = ws.nedge;
+  const unsigned mdin = __reduce_max_sync(FULL, ew);
+  if (w) {
+    const unsigned at = pw + __popc(wmask & ((1u << lane) - 1u));
+    w4_rows(B, warp)[at] = row;
+    slice(warp, 2)[at] = pe + eincl - ew;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    ws.nw4 = pw + kw;
+    ws.nedge = pe + esum;
+    ws.max_din = max(ws.max_din, mdin);
+  }
+  __syncwarp();
+}
+
+// Warp-collective, local rounds: lanes with pred remove u in round r (its G^T
+// row start and in-degree already loaded). A removal with at most LQ_DMAX
+// in-edges that fits this CTA's queue (buffer b) stays local: its G^T row is
+// copied into the queue now, all of the warp's rows at once (each lane loads
+// entries of the flattened rows, so the loads overlap). Everything else takes
+// the global path of an ordinary round (dead log, work list) and marks the
+// round as overflowing.
+__device__ __forceinline__ void local_append(const Dev& D, Cta& B, bool pred, uint32_t u,
+                                             uint32_t r, uint32_t row, uint32_t din,
+                                             uint32_t b) {
+  const unsigned lane = lane_id();
+  const unsigned mask = __ballot_sync(FULL, pred);
+  if (mask == 0u) return;
+  if (pred) D.level[u] = r;
+  const bool want = pred && din > 0u && din <= LQ_DMAX;
+  const unsigned wm = __ballot_sync(FULL, want);
+  bool ovf = pred && din > LQ_DMAX;
+  if (wm) {
+    const unsigned ew = want ? din : 0u;
+    const unsigned eincl = warp_incl_scan(ew);
+    const unsigned esum = __shfl_sync(FULL, eincl, 31);
+    const unsigned excl = eincl - ew;
+    const unsigned k = __popc(wm);
+    unsigned long long old = 0;
+    if (lane == 0)
+      old = atomicAdd(&B.lq_cnt[b], (unsigned long long)k | ((unsigned long long)esum << 32));
+    old = __shfl_sync(FULL, old, 0);
+    const uint32_t be = (uint32_t)old, bd = (uint32_t)(old >> 32);
+    if (be + k <= LQ_ENTRIES && bd + esum <= LQ_EDGES) {  // warp-uniform
+      if (lane == 0) atomicMax(&B.lq_vend[b], be + k);
+      if (want) {
+        const uint32_t slot = be + __popc(wm & ((1u << lane) - 1u));
+        B.lq_row[b][slot] = row;
+        B.lq_din[b][slot] = din;
+      }
+      // predecessors: element j of the flattened rows belongs to the lane with
+      // the largest exclusive prefix <= j; four loads in flight per lane
+      for (uint32_t j0 = 0; j0 < esum; j0 += 128u) {
+        uint32_t t[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t j = j0 + (uint32_t)q * 32u + lane;
+          const unsigned o = owner_of(excl, j);
+          const uint32_t ro = __shfl_sync(FULL, row, o), xo = __shfl_sync(FULL, excl, o);
+          t[q] = j < esum ? __ldg(&D.itgt[ro + (j - xo)]) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t j = j0 + (uint32_t)q * 32u + lane;
+          if (j < esum) B.lq_ids[b][bd + j] = t[q];
+        }
+      }
+    } else {
+      ovf = ovf || want;
+    }
+  }
+  const unsigned om = __ballot_sync(FULL, ovf);
+  if (lane == 0) {
+    atomicAdd(&B.lq_k, (unsigned)__popc(mask & ~om));
+    if (om) B.lq_ovf = 1u;
+  }
+  append_dead(D, B, ovf, u, r, D.live0, false, true, row, din);
+}
+#endif
+
 // End of round r: moves every warp slice of the CTA to global memory with one
 // global atomic per counter (all threads of the CTA). The (up to three) space
 // reservations are issued by three lanes at once, so they cost one round trip.
@@ -479,19 +621,6 @@ __device__ __forceinline__ void scan_warp_finish(const Dev& D, bool& resolved, u
   }
 }
 
-// Warp-collective search: owner lane j of element k, i.e. the largest j with
-// excl_j <= k (lanes that own nothing carry excl = total and are never picked).
-__device__ __forceinline__ unsigned owner_of(unsigned excl, unsigned k) {
-  unsigned lo = 0;
-#pragma unroll
-  for (unsigned step = 16; step >= 1; step >>= 1) {
-    const unsigned cand = lo + step;
-    const unsigned ex = __shfl_sync(FULL, excl, cand & 31u);
-    if (cand < 32u && ex <= k) lo = cand;
-  }
-  return lo;
-}
-
 // ------------------------------------------------------------------ scheduler
 
 __device__ __forceinline__ float log2p1(float x) { return log2f(1.0f + x); }
@@ -583,14 +712,18 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
   const bool logged = (D.flags & F_ROUND_LOG) && D.rlog != nullptr && r >= 1 && r - 1 < D.rlog_cap;
   // every value this step reads from the control block, issued together
   const uint32_t err = ld_relaxed(&C->err);
-  const uint32_t len = ld_relaxed(&C->log_len);
+  // removals so far: logged ones plus those counted only by local rounds
+  const uint32_t len = ld_relaxed(&C->log_len) + L.skew;
   const unsigned long long w4 = ld_relaxed64(&C->w4);
   const uint32_t live_count = ld_relaxed(&rs->live_count);
   const uint32_t max_din = ld_relaxed(&rs->max_din);
-  unsigned long long sum_in = 0, sum_out = 0, t_r = 0, t_rm1 = 0;
+  unsigned long long sum_in = 0, sum_out = 0, t_r = 0, t_rm1 = 0, local_edges = 0;
   uint32_t h0 = 0, h1 = 0, h2 = 0;
   const bool live_edges = feats || (D.flags & F_LIVE_EDGES);
-  if (live_edges) sum_out = ld_relaxed64(&rs->sum_out);
+  if (live_edges) {
+    sum_out = ld_relaxed64(&rs->sum_out);
+    local_edges = ld_relaxed64(&C->local_edges);
+  }
   if (feats) {
     sum_in = ld_relaxed64(&rs->sum_in);
     h0 = ld_relaxed(&rs->hist[0]);
@@ -635,6 +768,7 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
     D.roff[r] = L.fe;
     D.roff[r + 1] = len;
     C->rounds = nF ? r + 1 : r;
+    C->n_dead = len;
   }
   // live-edge count. With G^T and a complete AC-4 work list: edges between live
   // vertices = m minus the in-edges of removed vertices (a removed vertex has
@@ -642,7 +776,10 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
   // Otherwise: with G^T, the same from the in-degree sums; without it, out-edges
   // of live vertices (AC-3/AC-6 know each removed vertex's degree).
   if (live_edges) {
-    if (D.ioff != nullptr && (D.flags & F_AC4_POSSIBLE)) L.m_live = (unsigned long long)D.m - e_end;
+    // (in-edges pushed from local queues belong to removed vertices without
+    // work-list entries)
+    if (D.ioff != nullptr && (D.flags & F_AC4_POSSIBLE))
+      L.m_live = (unsigned long long)D.m - e_end - local_edges;
     else L.m_live -= (D.ioff != nullptr) ? sum_in : sum_out;
   }
   if (nF == 0) {
@@ -744,7 +881,9 @@ __device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_
   // and edge range come with one load, no chunk-owner lookup, and the warp
   // walks the entry's in-edges 32 at a time (at most 8 steps).
   if (ib - ia <= nwarps && eb - ea <= 32u * nwarps && S.bmax <= 256u) {
-    const uint32_t j = ia + gwarp;
+    // warp w of CTA c takes entry w * grid + c: a small round's entries (and
+    // the memory requests they cause) spread over every SM
+    const uint32_t j = ia + (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     if (j < ib) {
       const uint32_t row = ldcg(&D.w4_row[j]);
       const uint32_t eo = ldcg(&D.w4_eoff[j]);
@@ -800,6 +939,188 @@ __device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_
   }
   stats_flush(D, B, K);
 }
+
+#if TRIM_LOCAL
+// ------------------------------------------------------------------ local AC-4 rounds
+
+// Does round S.round start a stretch of local rounds? Its pending work-list
+// entries must make a small round (at most one entry per warp, none with more
+// than 256 in-edges); no per-round log is kept meanwhile.
+__device__ __forceinline__ bool local_start(const Dev& D, const Sched& S, uint32_t nwarps) {
+  if (D.local_edges_max == 0u || (D.flags & F_ROUND_LOG) || S.variant != TRIM_AC4_PUSH)
+    return false;
+  if (D.stop_round != 0u && S.round + 1u >= D.stop_round) return false;
+  const uint32_t items = S.w_end - S.c4w, edges = S.e_end - S.e_c4;
+  return items <= nwarps && edges <= 32u * nwarps && edges <= D.local_edges_max &&
+         S.bmax <= 256u;
+}
+
+// End of a local round (all threads): one arrival per CTA on the barrier word
+// of this round's parity, carrying 2^48 + 2^32 * (overflowed) + the CTA's local
+// removals; the wait ends when the word has grown by gridDim.x arrivals since
+// its value after its previous round (lbase), and that growth is the round's
+// totals. A slot is reused two rounds later, when every CTA has read it. The
+// wait is bounded like grid_barrier's. Returns false if it timed out.
+__device__ bool local_barrier(const Dev& D, Cta& B, uint32_t b) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Sched& S = B.S;
+    const uint32_t slot = S.lround & 1u;
+    if ((D.flags & F_LIVE_EDGES) && B.lq_pushed)
+      atomicAdd(&D.C->local_edges, (unsigned long long)B.lq_pushed);
+    const unsigned long long add =
+        (1ull << 48) | ((unsigned long long)B.lq_ovf << 32) | (unsigned long long)B.lq_k;
+    const unsigned long long base = S.lbase[slot];
+    fence_acq_rel();
+    red_relaxed_add64(&D.C->lbar[slot], add);
+    const uint64_t t0 = globaltimer();
+    unsigned long long cur = ld_acquire64(&D.C->lbar[slot]);
+    while ((uint32_t)((cur - base) >> 48) != gridDim.x) {
+      if (globaltimer() - t0 > D.spin_limit_ns) {
+        set_error(D, TRIM_ERR_TIMEOUT, 2);
+        B.err = TRIM_ERR_TIMEOUT;
+        break;
+      }
+      cur = ld_acquire64(&D.C->lbar[slot]);
+    }
+    B.lq_delta = cur - base;
+    S.lbase[slot] = cur;
+    S.lround += 1u;
+    // the next round fills the buffer this round read
+    B.lq_cnt[b ^ 1u] = 0ull;
+    B.lq_vend[b ^ 1u] = 0u;
+    B.lq_k = 0u;
+    B.lq_ovf = 0u;
+    B.lq_pushed = 0u;
+  }
+  __syncthreads();
+  return B.err == 0u;
+}
+
+// Thread 0: closes local round L.round, in which nF vertices were removed, all
+// of them counted only by the local barrier (the schedule step of advance()
+// for a round of the AC-4-only flavour, without reading the control block).
+__device__ void local_close(const Dev& D, Cta& B, uint32_t nF) {
+  Sched& L = B.S;
+  const uint32_t r = L.round;
+  L.vcount[TRIM_AC4_PUSH] += 1u;
+  L.c4w = L.w_end;  // the stretch's first round pushed every pending entry
+  L.e_c4 = L.e_end;
+  L.bmax = 0u;
+  L.skew += nF;
+  if (blockIdx.x == 0) {
+    D.C->vcount[TRIM_AC4_PUSH] = L.vcount[TRIM_AC4_PUSH];
+    D.C->rounds = nF ? r + 1u : r;
+    D.C->n_dead = L.fe + nF;
+  }
+  if (nF == 0u) {
+    L.done = 1u;
+    return;
+  }
+  L.stable = 0u;
+  L.prev_variant = TRIM_AC4_PUSH;
+  L.fprev = L.fe - L.fb;
+  L.round = r + 1u;
+  L.fb = L.fe;
+  L.fe += nF;
+}
+
+// Runs local rounds from round B.S.round on: the first pushes the pending
+// work-list entries (one per warp), later ones the predecessors in the CTA's
+// queue; every decrement loads the G^T row bounds of its vertex alongside the
+// atomic, so a removal costs no further dependent load before its row is
+// queued. The stretch ends when a round removes nothing (the run is done),
+// when a round overflowed the queues, or at the host's stop round; in the last
+// two cases the queued vertices join the global work list and the round ends
+// like an ordinary one (flush, grid barrier, advance). Returns false on a
+// timeout.
+__device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
+  Counters K;
+  const unsigned lane = lane_id();
+  bool first = true;
+  while (true) {
+    const uint32_t r = B.S.round;
+    const uint32_t b = B.S.lround & 1u;
+    const bool check = B.S.mixed;
+    start_round(D, r);
+    if (first) {
+      const uint32_t ia = B.S.c4w, ib = B.S.w_end, eb = B.S.e_end;
+      const uint32_t j = ia + (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+      if (j < ib) {  // warp-uniform
+        const uint32_t row = ldcg(&D.w4_row[j]);
+        const uint32_t eo = ldcg(&D.w4_eoff[j]);
+        const uint32_t ee = (j + 1u < ib) ? ldcg(&D.w4_eoff[j + 1u]) : eb;
+        for (uint32_t k0 = eo; k0 < ee; k0 += 32u) {
+          const uint32_t e = k0 + lane;
+          const bool valid = e < ee;
+          const uint32_t u = valid ? __ldg(&D.itgt[row + (e - eo)]) : 0u;
+          const uint32_t p0 = valid ? __ldg(&D.ioff[u]) : 0u;
+          const uint32_t p1 = valid ? __ldg(&D.ioff[u + 1u]) : 0u;
+          const uint32_t old = valid ? atomicSub(&D.cnt[u], 1u) : 0u;
+          K.pushed += valid ? 1u : 0u;
+          bool pred = valid && old == 1u;
+          if (pred && check) pred = ldcg(&D.level[u]) == LIVE;
+          local_append(D, B, pred, u, r, p0, p1 - p0, b);
+        }
+      }
+    } else {
+      const uint32_t qb = b ^ 1u;
+      const uint32_t qe = (uint32_t)(B.lq_cnt[qb] >> 32);
+      for (uint32_t base = 0; base < qe; base += 2u * blockDim.x) {  // CTA-uniform
+        uint32_t u[2], p0[2], p1[2], old[2];
+        bool valid[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint32_t k = base + (uint32_t)q * blockDim.x + threadIdx.x;
+          valid[q] = k < qe;
+          u[q] = valid[q] ? B.lq_ids[qb][k] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          p0[q] = valid[q] ? __ldg(&D.ioff[u[q]]) : 0u;
+          p1[q] = valid[q] ? __ldg(&D.ioff[u[q] + 1u]) : 0u;
+          old[q] = valid[q] ? atomicSub(&D.cnt[u[q]], 1u) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          K.pushed += valid[q] ? 1u : 0u;
+          bool pred = valid[q] && old[q] == 1u;
+          if (pred && check) pred = ldcg(&D.level[u[q]]) == LIVE;
+          local_append(D, B, pred, u[q], r, p0[q], p1[q] - p0[q], b);
+        }
+      }
+      if (threadIdx.x == 0) B.lq_pushed = qe;
+    }
+    if (!local_barrier(D, B, b)) break;
+    const unsigned long long d = B.lq_delta;
+    const uint32_t nF = (uint32_t)d, n_ovf = (uint32_t)(d >> 32) & 0xFFFFu;
+    const bool stop = D.stop_round != 0u && r + 1u >= D.stop_round;
+    if (n_ovf == 0u && (nF == 0u || !stop)) {
+      if (threadIdx.x == 0) local_close(D, B, nF);
+      __syncthreads();
+      first = false;
+      if (B.S.done) break;
+      continue;
+    }
+    // back to ordinary rounds: this round's queued vertices become work-list
+    // entries, and the round ends like an ordinary one
+    const uint32_t ne = B.lq_vend[b];
+    for (uint32_t i0 = (threadIdx.x >> 5) * 32u; i0 < ne; i0 += blockDim.x) {
+      const uint32_t i = i0 + lane;
+      const bool has = i < ne;
+      append_w4(D, B, has, has ? B.lq_row[b][i] : 0u, has ? B.lq_din[b][i] : 0u, r);
+    }
+    if (threadIdx.x == 0) B.S.skew += nF;
+    flush_round(D, B, r, D.live0);
+    if (!grid_barrier(D, B, false)) break;
+    if (threadIdx.x < 32) advance(D, B);
+    __syncthreads();
+    break;
+  }
+  stats_flush(D, B, K);
+  return B.err == 0u;
+}
+#endif
 
 // ------------------------------------------------------------------ AC-3
 
@@ -989,7 +1310,9 @@ __device__ ROUND_FN bool ac6_round(const Dev& D, Cta& B, const Sched& S, uint32_
   for (uint32_t base = S.fb + gwarp * G; base < S.fe; base += nwarps * G) {
     const uint32_t item = base + lane;
     const bool has = lane < G && item < S.fe;
-    const uint32_t w = has ? ldcg(&D.log[item]) : 0u;
+    // F_{r-1} was logged by an AC-6 round: its entries sit `skew` positions
+    // below their counts (removals counted only by local rounds are not logged)
+    const uint32_t w = has ? ldcg(&D.log[item - S.skew]) : 0u;
     uint32_t cur = has ? ldcg(&D.s_head[w]) : NIL;
     // bulk members of S(w): contiguous, spread over the lanes
     uint32_t ss = 0, sd = 0;
@@ -1105,6 +1428,9 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     S.bmax = 0;
     S.m_live = D.m;
     for (int i = 0; i < NFEAT; ++i) S.feat[i] = 0.0f;
+    S.skew = 0;
+    S.lround = 0;
+    S.lbase[0] = S.lbase[1] = 0;
 
     for (int w = 0; w < MAX_WARPS; ++w) {
       WarpSlice& x = B.ws[w];
@@ -1117,6 +1443,11 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     B.err = 0;
     B.w4_wide = 0;
     B.kstat[0] = B.kstat[1] = B.kstat[2] = B.kstat[3] = 0;
+#if TRIM_LOCAL
+    B.lq_cnt[0] = B.lq_cnt[1] = 0;
+    B.lq_vend[0] = B.lq_vend[1] = 0;
+    B.lq_k = B.lq_ovf = B.lq_pushed = 0;
+#endif
   }
 #if TRIM_MODES & 8
   // blob layout W1[32][12] b1 W2[32][32] b2 W3[3][32] b3 mean istd lo hi; W1 and
@@ -1180,6 +1511,13 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
       }
       break;
     }
+#if TRIM_LOCAL
+    if (local_start(D, S, nwarps)) {
+      if (!local_stretch(D, B)) break;
+      fresh = false;  // done, or the stretch's last round already ran advance()
+      continue;
+    }
+#endif
     start_round(D, S.round);
     if ((MODES & M_AC4) && S.variant == TRIM_AC4_PUSH) {
       ac4_round(D, B, S, gwarp, nwarps);

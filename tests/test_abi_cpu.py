@@ -39,12 +39,31 @@ def test_binding_declares_every_header_symbol(lib):
     assert set(declared_functions()) == bound
 
 
-def test_struct_layouts_match_header(lib):
+def test_struct_layouts_match_header(lib, tmp_path):
+    """Size and every field offset of the binding's structs equal what a C
+    compiler makes of include/trim.h."""
+    import subprocess
     from paper_2107_12720_gb300.abi import TrimCsr, TrimParams, TrimRoundRec, TrimRunStats
-    assert ctypes.sizeof(TrimCsr) == 40
-    assert ctypes.sizeof(TrimParams) == 32
-    assert ctypes.sizeof(TrimRunStats) == 64
-    assert ctypes.sizeof(TrimRoundRec) == 96
+    structs = {"trim_csr_t": TrimCsr, "trim_params_t": TrimParams,
+               "trim_run_stats_t": TrimRunStats, "trim_round_rec_t": TrimRoundRec}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "trim.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(root, "include"), str(src),
+                           "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln.strip())}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
 
 
 def test_host_argument_checks_without_device(lib):

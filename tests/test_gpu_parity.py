@@ -304,6 +304,50 @@ def test_commit_to_ac4_after_ac6_rounds():
             assert s["rounds_by_variant"][0] > 0 and s["rounds_by_variant"][1] > 0
 
 
+def test_local_rounds_match_ordinary_rounds():
+    """AC-4 with CTA-local rounds (the default once a round's pending work is
+    small) and without them (local_round_edges = 0) give the oracle's levels
+    and the same work counters, on every small workload and the hand cases
+    (a 5,000-in-edge hub overflows the local queues; chains stay local)."""
+    P = _P()
+    graphs = [cfg.config_small(i) for i in range(5)] + list(hand_cases().values())
+    for g in graphs:
+        lvl, st, alpha = oracle.peel(g.off, g.tgt)
+        with P.Trimmer(g.off, g.tgt, flags=P.TRIM_FLAG_STATS) as t:
+            s_local = t.run("ac4")
+            check(t, lvl, st, alpha, f"local-{g.name}", s_local)
+            t.set_params(local_round_edges=0)
+            s_plain = t.run("ac4")
+            check(t, lvl, st, alpha, f"plain-{g.name}", s_plain)
+            assert s_local["in_edges_pushed"] == s_plain["in_edges_pushed"], g.name
+            assert s_local["rounds_by_variant"] == s_plain["rounds_by_variant"] == [alpha, 0, 0] \
+                or alpha == 0
+            for edges in (1, 64, 4096):  # stretches entered at other thresholds
+                t.set_params(local_round_edges=edges)
+                check(t, lvl, st, alpha, f"local{edges}-{g.name}", t.run("ac4"))
+
+
+def test_committed_stretches_leave_local_rounds_at_the_stop_round():
+    """A scheduled run without a round log: its committed AC-4 stretches run
+    local rounds and must hand the run back to the scheduler exactly at the
+    stop round (queued vertices join the global work list), so the launch
+    count follows the commit rule and the levels equal the oracle's."""
+    P = _P()
+    for i, K, P0 in [(2, 4, 16), (2, 3, 5), (4, 2, 7), (0, 1, 3)]:
+        g = cfg.config_small(i)
+        lvl, st, alpha = oracle.peel(g.off, g.tgt)
+        off, tgt = dev_csr(g)
+        oi, ti = dev_csr_in(g)
+        with P.Trimmer(off, tgt, oi, ti, flags=P.TRIM_FLAG_STATS) as t:
+            t.set_params(sched_commit_rounds=K, sched_recheck_rounds=P0)
+            s = t.run("heuristic")
+            check(t, lvl, st, alpha, f"heuristic-commit[{i}]", s)
+            assert s["rounds_by_variant"] == [alpha, 0, 0]
+            assert s["segments"] == _commit_segments(alpha, K, P0), (i, s["segments"], alpha)
+            din = np.diff(oracle.transpose(g.off, g.tgt)[0].astype(np.int64))
+            assert s["in_edges_pushed"] == int(din[st == 0].sum())
+
+
 def _commit_segments(alpha, K, P0):
     """Launches of a scheduled run whose choice never changes: rounds 1..alpha;
     the choice has been kept for K rounds at the start of round K, where the run
