@@ -137,6 +137,7 @@ typedef struct {
   uint32_t rounds_by_variant[3]; /* rounds run by AC-4, AC-6, AC-3                         */
   uint32_t segments;        /* persistent-kernel launches of the run (1 unless a scheduled
                                trim_run switched between variant kernels)               */
+  uint32_t local_rounds;    /* AC-4 rounds that ran CTA-locally (see local_round_edges)   */
 } trim_run_stats_t;
 
 /* One record per round of a TRIM_FLAG_ROUND_LOG run. features[] are the

@@ -171,4 +171,5 @@ def _stats_dict(s: TrimRunStats) -> dict:
     return {"rounds": s.rounds, "n_dead": s.n_dead, "device_ms": s.device_ms,
             "edges_inspected": s.edges_inspected, "in_edges_pushed": s.in_edges_pushed,
             "candidates": s.candidates, "live_swept": s.live_swept,
-            "rounds_by_variant": list(s.rounds_by_variant), "segments": s.segments}
+            "rounds_by_variant": list(s.rounds_by_variant), "segments": s.segments,
+            "local_rounds": s.local_rounds}

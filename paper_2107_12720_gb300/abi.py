@@ -49,7 +49,7 @@ class TrimRunStats(ctypes.Structure):
                 ("device_ms", ctypes.c_float), ("edges_inspected", ctypes.c_uint64),
                 ("in_edges_pushed", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("live_swept", ctypes.c_uint64), ("rounds_by_variant", ctypes.c_uint32 * 3),
-                ("segments", ctypes.c_uint32)]
+                ("segments", ctypes.c_uint32), ("local_rounds", ctypes.c_uint32)]
 
 
 class TrimRoundRec(ctypes.Structure):

@@ -230,7 +230,7 @@ void default_params(trim_params_t* p) {
   p->spin_limit_ns = 5ull * 1000 * 1000 * 1000;  // 5 s
   p->heur_push_ratio = 1.0f;
   p->heur_ac6_ratio = 1.0f;
-  p->local_round_edges = 1u << 20;
+  p->local_round_edges = 1u << 18;
 }
 
 // per-warp append slices in dynamic shared memory: 4 buffers (dead log, AC-4
@@ -731,6 +731,7 @@ trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read) {
     s.live_swept = h.stats[3];
     for (int i = 0; i < 3; ++i) s.rounds_by_variant[i] = h.vcount[i];
     s.segments = (uint32_t)c->last_segments;
+    s.local_rounds = h.local_rounds;
     c->last = s;
     c->ran = true;
   }

@@ -95,7 +95,8 @@ struct Ctrl {
   alignas(128) unsigned long long lbar[2];  unsigned int _p4[28];
   unsigned long long local_edges; // in-edges pushed from the CTAs' local queues (live-edge count)
   unsigned int n_dead;            // removals so far, published by CTA 0
-  unsigned int _p5[29];
+  unsigned int local_rounds;      // local AC-4 rounds so far, published by CTA 0
+  unsigned int _p5[28];
   // segmented runs: a kernel that lacks the variant its scheduler picked saves
   // the schedule state here and exits; the kernel that has it resumes from it
   unsigned int resume;            // 1: a segment ended early, state in `saved`

@@ -533,13 +533,16 @@ __device__ bool grid_barrier(const Dev& D, Cta& B, bool read_err = true) {
     fence_acq_rel();
     red_relaxed_add(&D.C->bar, 1u);
     const uint64_t t0 = globaltimer();
-    while ((int)(ld_acquire(&D.C->bar) - target) < 0) {
+    // relaxed polls, then one acquiring load once every arrival is in (an
+    // acquiring load per poll would invalidate this SM's L1 every time)
+    while ((int)(ld_relaxed(&D.C->bar) - target) < 0) {
       if (globaltimer() - t0 > D.spin_limit_ns) {
         set_error(D, TRIM_ERR_TIMEOUT, 1);
         B.err = TRIM_ERR_TIMEOUT;
         break;
       }
     }
+    (void)ld_acquire(&D.C->bar);
     if (read_err) B.err = ld_relaxed(&D.C->err);
   }
   __syncthreads();
@@ -944,15 +947,14 @@ __device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_
 // ------------------------------------------------------------------ local AC-4 rounds
 
 // Does round S.round start a stretch of local rounds? Its pending work-list
-// entries must make a small round (at most one entry per warp, none with more
-// than 256 in-edges); no per-round log is kept meanwhile.
+// entries (the stretch's first round gives each warp whole entries) must have
+// at most local_edges_max in-edges in all, none more than 256.
 __device__ __forceinline__ bool local_start(const Dev& D, const Sched& S, uint32_t nwarps) {
-  if (D.local_edges_max == 0u || (D.flags & F_ROUND_LOG) || S.variant != TRIM_AC4_PUSH)
-    return false;
+  if (D.local_edges_max == 0u || S.variant != TRIM_AC4_PUSH) return false;
   if (D.stop_round != 0u && S.round + 1u >= D.stop_round) return false;
-  const uint32_t items = S.w_end - S.c4w, edges = S.e_end - S.e_c4;
-  return items <= nwarps && edges <= 32u * nwarps && edges <= D.local_edges_max &&
-         S.bmax <= 256u;
+  const uint32_t edges = S.e_end - S.e_c4;
+  (void)nwarps;
+  return edges <= D.local_edges_max && S.bmax <= 256u;
 }
 
 // End of a local round (all threads): one arrival per CTA on the barrier word
@@ -971,17 +973,23 @@ __device__ bool local_barrier(const Dev& D, Cta& B, uint32_t b) {
     const unsigned long long add =
         (1ull << 48) | ((unsigned long long)B.lq_ovf << 32) | (unsigned long long)B.lq_k;
     const unsigned long long base = S.lbase[slot];
-    fence_acq_rel();
+    // No fence before the arrival: across a local barrier CTAs exchange nothing
+    // through plain memory, only counter decrements, and every decrement of
+    // this round has returned its value (it is performed at L2) before this
+    // arrival is issued. Levels written here are read after the kernel or
+    // after an ordinary (fenced) barrier.
     red_relaxed_add64(&D.C->lbar[slot], add);
     const uint64_t t0 = globaltimer();
-    unsigned long long cur = ld_acquire64(&D.C->lbar[slot]);
+    // relaxed polls: an acquiring load would also invalidate this SM's L1 on
+    // every iteration, and nothing read after this barrier needs it
+    unsigned long long cur = ld_relaxed64(&D.C->lbar[slot]);
     while ((uint32_t)((cur - base) >> 48) != gridDim.x) {
       if (globaltimer() - t0 > D.spin_limit_ns) {
         set_error(D, TRIM_ERR_TIMEOUT, 2);
         B.err = TRIM_ERR_TIMEOUT;
         break;
       }
-      cur = ld_acquire64(&D.C->lbar[slot]);
+      cur = ld_relaxed64(&D.C->lbar[slot]);
     }
     B.lq_delta = cur - base;
     S.lbase[slot] = cur;
@@ -1009,9 +1017,24 @@ __device__ void local_close(const Dev& D, Cta& B, uint32_t nF) {
   L.bmax = 0u;
   L.skew += nF;
   if (blockIdx.x == 0) {
-    D.C->vcount[TRIM_AC4_PUSH] = L.vcount[TRIM_AC4_PUSH];
-    D.C->rounds = nF ? r + 1u : r;
-    D.C->n_dead = L.fe + nF;
+    Ctrl* C = D.C;
+    C->vcount[TRIM_AC4_PUSH] = L.vcount[TRIM_AC4_PUSH];
+    C->rounds = nF ? r + 1u : r;
+    C->n_dead = L.fe + nF;
+    C->local_rounds = L.lround;
+    if ((D.flags & F_ROUND_LOG) && D.rlog != nullptr && r >= 1u && r - 1u < D.rlog_cap) {
+      trim_round_rec_t* rec = &D.rlog[r - 1u];
+      rec->round = r;
+      rec->variant = TRIM_AC4_PUSH;
+      rec->frontier = L.fe - L.fb;
+      rec->removed = nF;
+      rec->t_start_ns = C->t_round[r & 3];
+      rec->t_end_ns = globaltimer();
+      rec->t_work_ns = C->t_work[r & 3];
+      rec->t_flush_ns = rec->t_work_ns;  // a local round moves nothing to global lists
+      for (int i = 0; i < NFEAT; ++i) rec->features[i] = 0.0f;
+      C->rlog_len = r;
+    }
   }
   if (nF == 0u) {
     L.done = 1u;
@@ -1045,8 +1068,8 @@ __device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
     start_round(D, r);
     if (first) {
       const uint32_t ia = B.S.c4w, ib = B.S.w_end, eb = B.S.e_end;
-      const uint32_t j = ia + (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-      if (j < ib) {  // warp-uniform
+      const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+      for (uint32_t j = ia + (threadIdx.x >> 5) * gridDim.x + blockIdx.x; j < ib; j += nw) {
         const uint32_t row = ldcg(&D.w4_row[j]);
         const uint32_t eo = ldcg(&D.w4_eoff[j]);
         const uint32_t ee = (j + 1u < ib) ? ldcg(&D.w4_eoff[j + 1u]) : eb;
@@ -1091,6 +1114,10 @@ __device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
       }
       if (threadIdx.x == 0) B.lq_pushed = qe;
     }
+    if ((D.flags & F_ROUND_LOG) && blockIdx.x == 0) {
+      __syncthreads();
+      if (threadIdx.x == 0) D.C->t_work[r & 3] = globaltimer();
+    }
     if (!local_barrier(D, B, b)) break;
     const unsigned long long d = B.lq_delta;
     const uint32_t nF = (uint32_t)d, n_ovf = (uint32_t)(d >> 32) & 0xFFFFu;
@@ -1110,8 +1137,13 @@ __device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
       const bool has = i < ne;
       append_w4(D, B, has, has ? B.lq_row[b][i] : 0u, has ? B.lq_din[b][i] : 0u, r);
     }
-    if (threadIdx.x == 0) B.S.skew += nF;
+    if (threadIdx.x == 0) {
+      B.S.skew += nF;
+      if (blockIdx.x == 0) D.C->local_rounds = B.S.lround;
+    }
     flush_round(D, B, r, D.live0);
+    if ((D.flags & F_ROUND_LOG) && blockIdx.x == 0 && threadIdx.x == 0)
+      D.C->t_flush[r & 3] = globaltimer();
     if (!grid_barrier(D, B, false)) break;
     if (threadIdx.x < 32) advance(D, B);
     __syncthreads();

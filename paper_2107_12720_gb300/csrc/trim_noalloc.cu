@@ -147,7 +147,7 @@ extern "C" trim_err_t trim_run_ac4_noalloc(const uint32_t* offsets, const uint32
   D.spin_limit_ns = 5ull * 1000 * 1000 * 1000;
   D.heur_push_ratio = 1.0f;
   D.heur_ac6_ratio = 1.0f;
-  D.local_edges_max = 1u << 20;  // as trim_run's default
+  D.local_edges_max = 1u << 18;  // as trim_run's default
 
   // The control block must start at zero; every other region is written
   // before it is read within a call, so stale contents of earlier calls are harmless.
