@@ -110,7 +110,8 @@ typedef struct {
                                  variant and continues on its single-variant kernel, with
                                  no feature or scheduling work (0 = never commit)        */
   uint32_t sched_recheck_rounds; /* ... a committed stretch lasts this many rounds, then the
-                                 scheduler is consulted again; each stretch that ends in
+                                 scheduler is consulted again for one round (keeping the
+                                 variant re-commits at once); each stretch that ends in
                                  the same commit doubles the next one                    */
   uint64_t spin_limit_ns;     /* bound of every device-side wait; past it the run stops
                                  with TRIM_ERR_TIMEOUT                                       */

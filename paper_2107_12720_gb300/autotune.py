@@ -11,7 +11,9 @@ and keeps, per variant, the fastest point:
   ctas_per_sm        as many as fit (0), or 1
   heur_push_ratio    0.5, 1, 2    (heuristic / learned fallback: AC-4 vs the rest)
   heur_ac6_ratio     0.5, 1, 2    (heuristic without G^T: AC-6 vs AC-3)
-  sched_commit_rounds 16, 32, 64  (scheduled runs: rounds before a commit)
+  sched_commit_rounds 4, 8, 32    (scheduled runs: rounds before a commit)
+  local_round_edges  0, 2^14, 2^18, 2^20 (AC-4: pending in-edges up to which rounds
+                     run CTA-locally)
 
 The launch shape is searched for every variant; the scheduler thresholds only
 for the heuristic and learned schedules (for which the launch shape is taken
@@ -39,7 +41,8 @@ TUNED_PATH = os.path.join(S.MODEL_DIR, "tuned_params.json")
 LAUNCH_SPACE = {"block_threads": (128, 256, 384, 512), "ctas_per_sm": (0, 1)}
 MIN_GAIN = 0.02  # a point must beat the best so far by 2% (timing noise is ~0.5%)
 SCHED_SPACE = {"heur_push_ratio": (0.5, 1.0, 2.0), "heur_ac6_ratio": (0.5, 1.0, 2.0),
-               "sched_commit_rounds": (16, 32, 64)}
+               "sched_commit_rounds": (4, 8, 32)}
+LOCAL_SPACE = {"local_round_edges": (0, 1 << 14, 1 << 18, 1 << 20)}
 
 
 def _points(space):
@@ -76,6 +79,14 @@ def tune(trimmer, variants=("ac4", "ac6", "ac3", "heuristic", "learned"), reps=5
                 log(f"{v:9s} {p} {ms:.4f} ms")
             if ms < best_ms * (1.0 - MIN_GAIN):
                 best, best_ms = p, ms
+        if v in ("ac4", "heuristic", "learned"):  # AC-4 runs (and committed AC-4 stretches)
+            for p in _points(LOCAL_SPACE):
+                q = {**best, **p}
+                ms = time_point(trimmer, v, q, reps)
+                if log:
+                    log(f"{v:9s} {q} {ms:.4f} ms")
+                if ms < best_ms * (1.0 - MIN_GAIN):
+                    best, best_ms = q, ms
         if v == "ac4":
             best_launch = dict(best)
         if v in ("heuristic", "learned"):

@@ -225,7 +225,7 @@ trim_err_t check_device(trim_ctx* c, int* dev, int* sms) {
 void default_params(trim_params_t* p) {
   p->block_threads = 512;
   p->ctas_per_sm = 0;
-  p->sched_commit_rounds = 32;
+  p->sched_commit_rounds = 8;
   p->sched_recheck_rounds = 128;
   p->spin_limit_ns = 5ull * 1000 * 1000 * 1000;  // 5 s
   p->heur_push_ratio = 1.0f;
@@ -658,8 +658,9 @@ trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read = fal
 // the heuristic or learned scheduler has kept its choice for
 // sched_commit_rounds rounds, the run commits: the next segment is the
 // single-variant kernel of that variant (no features, no scheduling) for
-// sched_recheck_rounds rounds, after which the scheduler is consulted again;
-// a stretch that ends in the same commit doubles the next one. The first
+// sched_recheck_rounds rounds, after which the scheduler is consulted again
+// for one round (if it keeps the variant, the run re-commits at once); a
+// stretch that ends in the same commit doubles the next one. The first
 // segment starts on the flavour this mode's last run started with.
 trim_err_t run_segmented(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats) {
   const int mi = (int)variant - (int)TRIM_SCHED_HEURISTIC;

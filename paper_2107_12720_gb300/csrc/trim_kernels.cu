@@ -132,7 +132,7 @@ struct Cta {
   uint32_t lq_k;                      // this round's removals kept local
   uint32_t lq_ovf;                    // 1: a removal of this round went to the global lists
   uint32_t lq_pushed;                 // predecessors decremented from the queue this round
-  unsigned long long lq_delta;        // the round's totals from the local barrier
+  uint32_t lq_next;                   // how the stretch goes on after the local barrier
 #endif
 };
 
@@ -825,9 +825,12 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
         if (in_range) next = learned;
       }
     }
-    // rounds in a row with an unchanged choice (a flavour without the
-    // schedulers makes no choice: a resumed scheduler starts counting afresh)
-    L.stable = !(MODES & M_SCHED) ? 0u : (r >= 1 && next == L.variant) ? L.stable + 1u : 1u;
+    // rounds in a row with an unchanged choice. A flavour without the
+    // schedulers makes no choice: it runs a committed stretch, and leaves the
+    // count one short of a commit, so that when the stretch ends one round in
+    // which the resumed scheduler confirms the variant re-commits the run.
+    L.stable = !(MODES & M_SCHED) ? (D.commit_after ? D.commit_after - 1u : 0u)
+               : (r >= 1 && next == L.variant) ? L.stable + 1u : 1u;
     L.prev_variant = (r >= 1) ? L.variant : NIL;
     L.fprev = L.fe - L.fb;  // frontier of round r, for the timing feature two rounds on
     L.variant = next;
@@ -957,54 +960,6 @@ __device__ __forceinline__ bool local_start(const Dev& D, const Sched& S, uint32
   return edges <= D.local_edges_max && S.bmax <= 256u;
 }
 
-// End of a local round (all threads): one arrival per CTA on the barrier word
-// of this round's parity, carrying 2^48 + 2^32 * (overflowed) + the CTA's local
-// removals; the wait ends when the word has grown by gridDim.x arrivals since
-// its value after its previous round (lbase), and that growth is the round's
-// totals. A slot is reused two rounds later, when every CTA has read it. The
-// wait is bounded like grid_barrier's. Returns false if it timed out.
-__device__ bool local_barrier(const Dev& D, Cta& B, uint32_t b) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    Sched& S = B.S;
-    const uint32_t slot = S.lround & 1u;
-    if ((D.flags & F_LIVE_EDGES) && B.lq_pushed)
-      atomicAdd(&D.C->local_edges, (unsigned long long)B.lq_pushed);
-    const unsigned long long add =
-        (1ull << 48) | ((unsigned long long)B.lq_ovf << 32) | (unsigned long long)B.lq_k;
-    const unsigned long long base = S.lbase[slot];
-    // No fence before the arrival: across a local barrier CTAs exchange nothing
-    // through plain memory, only counter decrements, and every decrement of
-    // this round has returned its value (it is performed at L2) before this
-    // arrival is issued. Levels written here are read after the kernel or
-    // after an ordinary (fenced) barrier.
-    red_relaxed_add64(&D.C->lbar[slot], add);
-    const uint64_t t0 = globaltimer();
-    // relaxed polls: an acquiring load would also invalidate this SM's L1 on
-    // every iteration, and nothing read after this barrier needs it
-    unsigned long long cur = ld_relaxed64(&D.C->lbar[slot]);
-    while ((uint32_t)((cur - base) >> 48) != gridDim.x) {
-      if (globaltimer() - t0 > D.spin_limit_ns) {
-        set_error(D, TRIM_ERR_TIMEOUT, 2);
-        B.err = TRIM_ERR_TIMEOUT;
-        break;
-      }
-      cur = ld_relaxed64(&D.C->lbar[slot]);
-    }
-    B.lq_delta = cur - base;
-    S.lbase[slot] = cur;
-    S.lround += 1u;
-    // the next round fills the buffer this round read
-    B.lq_cnt[b ^ 1u] = 0ull;
-    B.lq_vend[b ^ 1u] = 0u;
-    B.lq_k = 0u;
-    B.lq_ovf = 0u;
-    B.lq_pushed = 0u;
-  }
-  __syncthreads();
-  return B.err == 0u;
-}
-
 // Thread 0: closes local round L.round, in which nF vertices were removed, all
 // of them counted only by the local barrier (the schedule step of advance()
 // for a round of the AC-4-only flavour, without reading the control block).
@@ -1040,12 +995,73 @@ __device__ void local_close(const Dev& D, Cta& B, uint32_t nF) {
     L.done = 1u;
     return;
   }
-  L.stable = 0u;
+  L.stable = D.commit_after ? D.commit_after - 1u : 0u;  // as advance() in this flavour
   L.prev_variant = TRIM_AC4_PUSH;
   L.fprev = L.fe - L.fb;
   L.round = r + 1u;
   L.fb = L.fe;
   L.fe += nF;
+}
+
+// End of local round r (all threads): one arrival per CTA on the barrier word
+// of this round's parity, carrying 2^48 + 2^32 * (overflowed) + the CTA's local
+// removals; the wait ends when the word has grown by gridDim.x arrivals since
+// its value after its previous round (lbase), and that growth is the round's
+// totals. A slot is reused two rounds later, when every CTA has read it. The
+// wait is bounded like grid_barrier's. Thread 0 then decides how the stretch
+// goes on (B.lq_next: LQ_GO on, LQ_DONE the run is over, both after closing
+// the round; LQ_LEAVE back to ordinary rounds). Returns false on a timeout.
+constexpr uint32_t LQ_GO = 0, LQ_DONE = 1, LQ_LEAVE = 2;
+__device__ bool local_barrier(const Dev& D, Cta& B, uint32_t b, uint32_t r) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Sched& S = B.S;
+    const uint32_t slot = S.lround & 1u;
+    if ((D.flags & F_LIVE_EDGES) && B.lq_pushed)
+      atomicAdd(&D.C->local_edges, (unsigned long long)B.lq_pushed);
+    const unsigned long long add =
+        (1ull << 48) | ((unsigned long long)B.lq_ovf << 32) | (unsigned long long)B.lq_k;
+    const unsigned long long base = S.lbase[slot];
+    // No fence before the arrival: across a local barrier CTAs exchange nothing
+    // through plain memory, only counter decrements, and every decrement of
+    // this round has returned its value (it is performed at L2) before this
+    // arrival is issued. Levels written here are read after the kernel or
+    // after an ordinary (fenced) barrier.
+    red_relaxed_add64(&D.C->lbar[slot], add);
+    const uint64_t t0 = globaltimer();
+    // relaxed polls: an acquiring load would also invalidate this SM's L1 on
+    // every iteration, and nothing read after this barrier needs it
+    unsigned long long cur = ld_relaxed64(&D.C->lbar[slot]);
+    while ((uint32_t)((cur - base) >> 48) != gridDim.x) {
+      if (globaltimer() - t0 > D.spin_limit_ns) {
+        set_error(D, TRIM_ERR_TIMEOUT, 2);
+        B.err = TRIM_ERR_TIMEOUT;
+        break;
+      }
+      cur = ld_relaxed64(&D.C->lbar[slot]);
+    }
+    const unsigned long long d = cur - base;
+    S.lbase[slot] = cur;
+    S.lround += 1u;
+    const uint32_t nF = (uint32_t)d, n_ovf = (uint32_t)(d >> 32) & 0xFFFFu;
+    const bool stop = D.stop_round != 0u && r + 1u >= D.stop_round;
+    if (n_ovf == 0u && (nF == 0u || !stop)) {
+      local_close(D, B, nF);  // every removal of the round is in the queues
+      B.lq_next = nF ? LQ_GO : LQ_DONE;
+    } else {
+      S.skew += nF;  // advance() closes the round after the work-list handover
+      if (blockIdx.x == 0) D.C->local_rounds = S.lround;
+      B.lq_next = LQ_LEAVE;
+    }
+    // the next round fills the buffer this round read
+    B.lq_cnt[b ^ 1u] = 0ull;
+    B.lq_vend[b ^ 1u] = 0u;
+    B.lq_k = 0u;
+    B.lq_ovf = 0u;
+    B.lq_pushed = 0u;
+  }
+  __syncthreads();
+  return B.err == 0u;
 }
 
 // Runs local rounds from round B.S.round on: the first pushes the pending
@@ -1118,15 +1134,11 @@ __device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
       __syncthreads();
       if (threadIdx.x == 0) D.C->t_work[r & 3] = globaltimer();
     }
-    if (!local_barrier(D, B, b)) break;
-    const unsigned long long d = B.lq_delta;
-    const uint32_t nF = (uint32_t)d, n_ovf = (uint32_t)(d >> 32) & 0xFFFFu;
-    const bool stop = D.stop_round != 0u && r + 1u >= D.stop_round;
-    if (n_ovf == 0u && (nF == 0u || !stop)) {
-      if (threadIdx.x == 0) local_close(D, B, nF);
-      __syncthreads();
+    if (!local_barrier(D, B, b, r)) break;
+    const uint32_t next = B.lq_next;
+    if (next == LQ_DONE) break;
+    if (next == LQ_GO) {
       first = false;
-      if (B.S.done) break;
       continue;
     }
     // back to ordinary rounds: this round's queued vertices become work-list
@@ -1136,10 +1148,6 @@ __device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
       const uint32_t i = i0 + lane;
       const bool has = i < ne;
       append_w4(D, B, has, has ? B.lq_row[b][i] : 0u, has ? B.lq_din[b][i] : 0u, r);
-    }
-    if (threadIdx.x == 0) {
-      B.S.skew += nF;
-      if (blockIdx.x == 0) D.C->local_rounds = B.S.lround;
     }
     flush_round(D, B, r, D.live0);
     if ((D.flags & F_ROUND_LOG) && blockIdx.x == 0 && threadIdx.x == 0)

@@ -33,15 +33,17 @@ def lib_available():
 def test_tune_finds_the_minimum(lib_available):
     def cost(v, p):
         c = 1.0 + abs(p["block_threads"] - 384) / 1000 + 0.1 * p["ctas_per_sm"]
+        c += 0.05 * (p["local_round_edges"] != (1 << 14))
         if v == "heuristic":
-            c += abs(p["heur_push_ratio"] - 2.0) + abs(p["sched_commit_rounds"] - 16) / 100
+            c += abs(p["heur_push_ratio"] - 2.0) + abs(p["sched_commit_rounds"] - 32) / 100
         return c
     t = FakeTrimmer(cost)
     res = A.tune(t, variants=("ac4", "heuristic"), reps=1)
-    assert res["ac4"]["params"] == {"block_threads": 384, "ctas_per_sm": 0}
+    assert res["ac4"]["params"] == {"block_threads": 384, "ctas_per_sm": 0,
+                                    "local_round_edges": 1 << 14}
     hp = res["heuristic"]["params"]
-    assert hp["heur_push_ratio"] == 2.0 and hp["sched_commit_rounds"] == 16
-    assert hp["block_threads"] == 384
+    assert hp["heur_push_ratio"] == 2.0 and hp["sched_commit_rounds"] == 32
+    assert hp["block_threads"] == 384 and hp["local_round_edges"] == 1 << 14
     assert res["heuristic"]["ms"] < res["heuristic"]["default_ms"]
 
 

@@ -352,7 +352,8 @@ def _commit_segments(alpha, K, P0):
     """Launches of a scheduled run whose choice never changes: rounds 1..alpha;
     the choice has been kept for K rounds at the start of round K, where the run
     commits; a stretch from round r runs to the start of round r+p (p = P0,
-    doubling); the scheduler then counts K rounds afresh before committing."""
+    doubling); the scheduler then runs round r+p and, keeping its choice,
+    re-commits at the start of round r+p+1."""
     segs, r, p = 1, K, P0
     if r > alpha:
         return segs
@@ -361,8 +362,8 @@ def _commit_segments(alpha, K, P0):
         end = r + p
         if end > alpha:          # the run ends inside the stretch
             return segs
-        segs += 1                # scheduler kernel from round `end`
-        r = end + K
+        segs += 1                # scheduler kernel for round `end`
+        r = end + 1
         if r > alpha:
             return segs
         p *= 2
