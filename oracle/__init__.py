@@ -55,6 +55,11 @@ def _L():
             lib.or_ac3.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u8p]
             lib.or_certificate.restype = ctypes.c_int64
             lib.or_certificate.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u8p]
+            lib.or_peel_inout.restype = ctypes.c_uint32
+            lib.or_peel_inout.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u32p, u32p, u8p]
+            lib.or_certificate_inout.restype = ctypes.c_int64
+            lib.or_certificate_inout.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u32p, u32p,
+                                                 u8p]
             _lib = lib
     return _lib
 
@@ -122,3 +127,30 @@ def certificate(off, tgt, level, status) -> int:
     if n == 0:
         return -1
     return int(_L().or_certificate(n, off, tgt, level, status))
+
+
+def peel_inout(off, tgt, csr_in=None):
+    """In+out trimming (removal on no live successor or no live predecessor, one
+    peeling step at a time; see or_peel_inout). Returns (level, status, alpha)."""
+    off, tgt = _csr(off, tgt)
+    n = off.shape[0] - 1
+    off_in, tgt_in = transpose(off, tgt) if csr_in is None else csr_in
+    off_in, tgt_in = _csr(off_in, tgt_in)
+    level = np.empty(max(n, 1), np.uint32)
+    status = np.empty(max(n, 1), np.uint8)
+    alpha = _L().or_peel_inout(n, off, tgt, off_in, tgt_in, level, status)
+    return level[:n], status[:n], int(alpha)
+
+
+def certificate_inout(off, tgt, level, status, csr_in=None) -> int:
+    """-1 if (level, status) is the in+out trimming result of the graph, else the
+    first vertex that violates a local condition (see or_certificate_inout)."""
+    off, tgt = _csr(off, tgt)
+    n = off.shape[0] - 1
+    if n == 0:
+        return -1
+    off_in, tgt_in = transpose(off, tgt) if csr_in is None else csr_in
+    off_in, tgt_in = _csr(off_in, tgt_in)
+    level = np.ascontiguousarray(level, np.uint32)
+    status = np.ascontiguousarray(status, np.uint8)
+    return int(_L().or_certificate_inout(n, off, tgt, off_in, tgt_in, level, status))

@@ -24,6 +24,10 @@
  *   or_ac3         O3: AC-3-based trimming (Algorithm 4) with one snapshot per
  *                  repetition (every repetition reads the previous one's status)
  *   or_certificate local conditions that hold for exactly one assignment
+ *   or_peel_inout  in+out trimming (the in-degree check of Section 4's remark on
+ *                  AC-3 with G^T loaded): removal on no live successor OR no
+ *                  live predecessor, one peeling step at a time
+ *   or_certificate_inout  its local conditions (exactly one assignment)
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -206,6 +210,98 @@ int64_t or_certificate(uint32_t n, const uint32_t* off, const uint32_t* tgt,
         if (lw + 1 > want) want = lw + 1;
       }
       if (level[v] != want) return v;
+    }
+  }
+  return -1;
+}
+
+/* In+out trimming. Section 4 remarks that with G^T in memory each vertex must
+ * also keep at least one available incoming edge, which trims more size-1 SCCs
+ * (the form FW-BW and ISPAN use, Section 1). The process is Definition 2's with
+ * both conditions: step 0 removes every vertex without out-edges or without
+ * in-edges; step r removes every vertex still present with no successor or no
+ * predecessor among the vertices present after step r-1. Here, as in or_peel,
+ * two counters per vertex count its successors and predecessors still present;
+ * every vertex removed in step r-1 decrements the out-counter of each
+ * predecessor and the in-counter of each successor (once per parallel edge),
+ * and a present vertex whose counter reaches zero is removed in step r.
+ * Returns alpha (the number of steps that removed something). */
+uint32_t or_peel_inout(uint32_t n, const uint32_t* off, const uint32_t* tgt,
+                       const uint32_t* off_in, const uint32_t* tgt_in, uint32_t* level,
+                       uint8_t* status) {
+  uint32_t* cnt_out = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4);
+  uint32_t* cnt_in = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4);
+  uint32_t* cur = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4);
+  uint32_t* nxt = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4);
+  uint32_t ncur = 0, alpha = 0;
+  for (uint32_t v = 0; v < n; ++v) {
+    cnt_out[v] = off[v + 1] - off[v];
+    cnt_in[v] = off_in[v + 1] - off_in[v];
+    level[v] = LIVE;
+    if (cnt_out[v] == 0 || cnt_in[v] == 0) { level[v] = 0; cur[ncur++] = v; }
+  }
+  for (uint32_t r = 1; ncur > 0; ++r) {
+    alpha = r;
+    uint32_t nnxt = 0;
+    for (uint32_t i = 0; i < ncur; ++i) {
+      uint32_t w = cur[i];
+      for (uint32_t e = off_in[w]; e < off_in[w + 1]; ++e) {  /* w's predecessors */
+        uint32_t u = tgt_in[e];
+        if (level[u] != LIVE) continue;
+        cnt_out[u] -= 1;
+        if (cnt_out[u] == 0) { level[u] = r; nxt[nnxt++] = u; }
+      }
+      for (uint32_t e = off[w]; e < off[w + 1]; ++e) {  /* w's successors */
+        uint32_t s = tgt[e];
+        if (level[s] != LIVE) continue;
+        cnt_in[s] -= 1;
+        if (cnt_in[s] == 0) { level[s] = r; nxt[nnxt++] = s; }
+      }
+    }
+    uint32_t* t = cur; cur = nxt; nxt = t; ncur = nnxt;
+  }
+  for (uint32_t v = 0; v < n; ++v) status[v] = (level[v] == LIVE);
+  free(cnt_out); free(cnt_in); free(cur); free(nxt);
+  return alpha;
+}
+
+/* Certificate of in+out trimming. With t_out(v) = 0 if v has no successor, else
+ * 1 + the largest successor level if every successor is DEAD, else infinity;
+ * and t_in(v) the same over predecessors:
+ *  (i)  every LIVE v has a LIVE successor and a LIVE predecessor;
+ *  (ii) every DEAD v has level[v] = min(t_out(v), t_in(v)) (finite);
+ *  (iii) status and level agree.
+ * (i) makes the LIVE set a subgraph in which every vertex keeps an in- and an
+ * out-edge; by (ii), induction on the level shows that no DEAD vertex belongs
+ * to such a subgraph and that the vertices of each level are exactly those the
+ * process removes in that step. Returns -1 if all hold, else the first
+ * violating vertex. */
+int64_t or_certificate_inout(uint32_t n, const uint32_t* off, const uint32_t* tgt,
+                             const uint32_t* off_in, const uint32_t* tgt_in,
+                             const uint32_t* level, const uint8_t* status) {
+  const uint64_t INF = 0xFFFFFFFFFFull;
+  for (uint32_t v = 0; v < n; ++v) {
+    int is_live = status[v] != 0;
+    if (is_live != (level[v] == LIVE)) return v;
+    int live_succ = 0, live_pred = 0;
+    uint64_t t_out = 0, t_in = 0;
+    for (uint32_t e = off[v]; e < off[v + 1]; ++e) {
+      uint32_t lw = level[tgt[e]];
+      if (lw == LIVE) live_succ = 1;
+      else if ((uint64_t)lw + 1 > t_out) t_out = (uint64_t)lw + 1;
+    }
+    for (uint32_t e = off_in[v]; e < off_in[v + 1]; ++e) {
+      uint32_t lu = level[tgt_in[e]];
+      if (lu == LIVE) live_pred = 1;
+      else if ((uint64_t)lu + 1 > t_in) t_in = (uint64_t)lu + 1;
+    }
+    if (live_succ) t_out = INF;
+    if (live_pred) t_in = INF;
+    if (is_live) {
+      if (!live_succ || !live_pred) return v;
+    } else {
+      uint64_t want = t_out < t_in ? t_out : t_in;
+      if (want == INF || level[v] != want) return v;
     }
   }
   return -1;
