@@ -364,6 +364,8 @@ def time_variant(P, t, variant, steps, warmup, flush_buf, graph_off=None):
     import torch
     stream = t.stream
     run = (lambda: t.batch_run(graph_off, variant)) if graph_off is not None else None
+    if variant == "inout":  # in+out trimming (another problem on the same graph)
+        run = t.run_inout
     for _ in range(warmup):
         run() if run else t.run(variant)
     times, kern = [], []
@@ -499,7 +501,8 @@ def extra_workload(P, idx, args, flush, stream, model):
     bufs = [dev(g.off), dev(g.tgt), dev(oi), dev(ti)]
     batched = idx == 3
     gofs = g.graph_off if batched else None
-    names = ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if model is not None else [])
+    names = ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if model is not None else []) \
+        + ([] if batched else ["inout"])
     with P.Trimmer(*bufs, stream=stream) as t:
         if model is not None:
             t.set_model(model)
@@ -555,7 +558,8 @@ def run_ours(args, rank, ws, local):
             # AC-3 sweeps the live set every round: on the 10,004-round large
             # graph that is hours of work, so it is left out there
             names = (["ac4", "ac6"] + ([] if args.config == 4 and not args.small else ["ac3"])
-                     + ["heuristic"] + (["learned"] if model is not None else []))
+                     + ["heuristic"] + (["learned"] if model is not None else [])
+                     + ([] if batched else ["inout"]))
         sweep = sweep_variants(P, t, g, args, key, names, flush, gofs)
 
     tuned = apply_tuned(t, args, headline, key)

@@ -187,6 +187,25 @@ trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void
  * that trim_run_async uses. */
 trim_err_t trim_run(trim_ctx* ctx, trim_variant_t variant, trim_run_stats_t* stats);
 
+/* In+out trimming: removes every vertex that has no live successor OR no live
+ * predecessor, repeatedly (Section 4's remark on checking the in-degree when
+ * the transposed graph is in memory; Section 1: the size-1 SCC trimming that
+ * FW-BW and ISPAN run before and after large-SCC detection). Step 0 removes
+ * the vertices without out-edges or without in-edges; step r removes every
+ * vertex still present that has no successor or no predecessor among the
+ * vertices present after step r-1, and trim_level reports that step (the
+ * smaller of the vertex's Definition-2 levels in G and in G^T). Survivors are
+ * exactly the vertices that reach a directed cycle and are reached from one.
+ * Needs G^T (csr_in, or built on the device on first use, outside the timing).
+ * Runs as one persistent launch that pushes, for every removed vertex, both
+ * its G^T row (out-degree counters of its predecessors) and its G row
+ * (in-degree counters of its successors). Results are read with trim_status /
+ * trim_level like those of trim_run; stats may be NULL (in_edges_pushed counts
+ * the G^T pushes, edges_inspected the G pushes). Graphs with 2m > 2^32 - 64 are
+ * refused with TRIM_ERR_TOO_LARGE (the work list counts both rows of a vertex in
+ * uint32 edge offsets). */
+trim_err_t trim_run_inout(trim_ctx* ctx, trim_run_stats_t* stats);
+
 /* Enqueues the same work as trim_run without waiting (no host synchronisation,
  * so it may be captured into a CUDA graph): one persistent launch, for a
  * scheduled run that of the kernel holding all three variants. Errors raised on the device surface

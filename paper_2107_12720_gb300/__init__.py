@@ -24,7 +24,8 @@ from .abi import (LIB_PATH, TRIM_AC3_PULL, TRIM_AC4_PUSH, TRIM_AC6_SUPPORT, TRIM
 from .abi import (trim_batch_run, trim_create, trim_default_params, trim_destroy,
                   trim_get_params, trim_get_round_log, trim_last_error, trim_level,
                   trim_level_device_ptr, trim_mlp_adam_step, trim_mlp_forward, trim_mlp_loss_grad,
-                  trim_mlp_scratch_bytes, trim_run, trim_run_async, trim_set_alloc_limit,
+                  trim_mlp_scratch_bytes, trim_run, trim_run_async, trim_run_inout,
+                  trim_set_alloc_limit,
                   trim_set_model, trim_set_params, trim_set_schedule, trim_status, trim_sync)
 
 VARIANTS = {"ac4": TRIM_AC4_PUSH, "ac6": TRIM_AC6_SUPPORT, "ac3": TRIM_AC3_PULL,
@@ -98,6 +99,11 @@ class Trimmer:
 
     def run(self, variant="ac4") -> dict:
         return _stats_dict(trim_run(self.ctx, _variant(variant)))
+
+    def run_inout(self) -> dict:
+        """In+out trimming (no live successor or no live predecessor removes a
+        vertex); results through level() and status() as after run()."""
+        return _stats_dict(trim_run_inout(self.ctx))
 
     def run_async(self, variant="ac4") -> None:
         trim_run_async(self.ctx, _variant(variant))

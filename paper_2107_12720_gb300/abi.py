@@ -67,6 +67,7 @@ SIGNATURES = [
     ("trim_create", _I, [ctypes.POINTER(TrimCsr), ctypes.POINTER(TrimCsr), _P, _U32,
                          ctypes.POINTER(_P)]),
     ("trim_run", _I, [_P, _I, ctypes.POINTER(TrimRunStats)]),
+    ("trim_run_inout", _I, [_P, ctypes.POINTER(TrimRunStats)]),
     ("trim_run_async", _I, [_P, _I]),
     ("trim_sync", _I, [_P, ctypes.POINTER(TrimRunStats)]),
     ("trim_status", _I, [_P, _P, _I]),
@@ -137,6 +138,12 @@ def trim_create(csr_out: TrimCsr, csr_in, stream, flags: int):
 def trim_run(ctx, variant: int) -> TrimRunStats:
     s = TrimRunStats()
     check(lib().trim_run(ctx, variant, ctypes.byref(s)), ctx)
+    return s
+
+
+def trim_run_inout(ctx) -> TrimRunStats:
+    s = TrimRunStats()
+    check(lib().trim_run_inout(ctx, ctypes.byref(s)), ctx)
     return s
 
 

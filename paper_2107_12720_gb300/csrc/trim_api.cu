@@ -41,6 +41,9 @@ struct trim_ctx {
            *s_next = nullptr, *s_cnt = nullptr, *s_off = nullptr, *s_list = nullptr,
            *log = nullptr, *roff = nullptr, *live0 = nullptr, *live1 = nullptr, *bsum = nullptr;
   uint32_t *w4_row = nullptr, *w4_eoff = nullptr, *chunk_first = nullptr;
+  // in+out runs: in-degree counters, the work list's G rows and in-degrees, and
+  // the chunk-owner index of its edge space (both rows: up to 2m edges)
+  uint32_t *cnt_in = nullptr, *w4_orow = nullptr, *w4_din = nullptr, *chunk_io = nullptr;
   Ctrl* ctrl = nullptr;
   Ctrl* h_ctrl = nullptr;  // host mirror of the control block for read-back
   bool h_ctrl_pinned = false;
@@ -52,7 +55,7 @@ struct trim_ctx {
   uint32_t script_len = 0;
   uint8_t* status_tmp = nullptr;
   trim_params_t params{};
-  int grids[7] = {0, 0, 0, 0, 0, 0, 0};  // cooperative grid size of each kernel flavour
+  int grids[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // cooperative grid size of each kernel flavour
   trimk::Dev last_dev{};        // arguments of the last launch (segments reuse them)
   int seg_first[3] = {-1, -1, -1};  // per scheduled mode: flavour of its last first round
   uint64_t last_segments = 0;       // kernel launches of the last trim_run
@@ -243,15 +246,17 @@ size_t dyn_smem_bytes(uint32_t block_threads) {
 }
 
 // kernel flavours: index 0..3 = AC-4 only, AC-6 only, AC-3 only, everything;
-// 4..6 = AC-4, AC-6, AC-3 each with the per-round schedulers (segments)
+// 4..6 = AC-4, AC-6, AC-3 each with the per-round schedulers (segments);
+// 7 = in+out trimming
 typedef void (*persistent_fn)(trimk::Dev);
-constexpr int kNumFlavours = 7;
+constexpr int kNumFlavours = 8;
 constexpr int kFlavourAll = 3;
 constexpr int kFlavourSeg = 4;  // + variant
+constexpr int kFlavourInout = 7;
 const persistent_fn kFlavours[kNumFlavours] = {
     trim_persistent_kernel_m1,  trim_persistent_kernel_m2,  trim_persistent_kernel_m4,
     trim_persistent_kernel_m15, trim_persistent_kernel_m9,  trim_persistent_kernel_m10,
-    trim_persistent_kernel_m12};
+    trim_persistent_kernel_m12, trim_persistent_kernel_m17};
 
 // launch shapes are a property of the device and the block size: computed once
 // per (device, block_threads, ctas_per_sm) for the whole process
@@ -536,12 +541,31 @@ trim_err_t ensure_work_list(trim_ctx* c) {
   return TRIM_OK;
 }
 
+// In+out trimming's arrays: in-degree counters and the work list's out-CSR
+// row starts and in-degrees; allocated on first use.
+trim_err_t ensure_inout(trim_ctx* c) {
+  if (c->cnt_in) return TRIM_OK;
+  // the work list's edge offsets are uint32 and cover both rows of every vertex
+  if (2 * c->m > (1ull << 32) - 64)
+    return fail(c, TRIM_ERR_TOO_LARGE, "in+out trimming needs 2m <= 2^32 - 64");
+  TRY(dalloc(c, &c->cnt_in, c->n));
+  TRY(dalloc(c, &c->w4_orow, c->n));
+  TRY(dalloc(c, &c->w4_din, c->n));
+  TRY(dalloc(c, &c->chunk_io, ((2 * c->m) >> 5) + 2));
+  return TRIM_OK;
+}
+
 // Enqueues one run. A scheduled variant runs on the all-variant kernel, or with
 // seg_flavour >= 0 as the first segment of a segmented run (run_segmented).
+// With inout, the run is in+out trimming (variant must be TRIM_AC4_PUSH).
 trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1,
-                       uint32_t commit_after = 0) {
+                       uint32_t commit_after = 0, bool inout = false) {
   if ((int)variant < 0 || variant > TRIM_SCHED_SCRIPTED)
     return fail(c, TRIM_ERR_INVALID_ARG, "unknown variant");
+  if (inout) {
+    if (c->ioff == nullptr) TRY(build_transpose(c));
+    TRY(ensure_inout(c));
+  }
   if (variant == TRIM_SCHED_SCRIPTED && c->script_len == 0)
     return fail(c, TRIM_ERR_STATE, "TRIM_SCHED_SCRIPTED needs trim_set_schedule first");
   if (variant == TRIM_AC4_PUSH && c->ioff == nullptr) TRY(build_transpose(c));
@@ -592,6 +616,8 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   D.s_list = c->s_list; D.log = c->log; D.roff = c->roff; D.live0 = c->live0;
   D.live1 = c->live1; D.w4_row = c->w4_row; D.w4_eoff = c->w4_eoff;
   D.chunk_first = c->chunk_first; D.bsum = c->bsum; D.C = c->ctrl;
+  D.cnt_in = c->cnt_in; D.w4_orow = c->w4_orow; D.w4_din = c->w4_din;
+  if (inout) D.chunk_first = c->chunk_io;
   D.sbuf_cap = kSbufCap;
   D.rlog = c->rlog; D.rlog_cap = c->rlog_cap;
   D.model = c->has_model ? c->model : nullptr;
@@ -607,7 +633,8 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   if (variant >= TRIM_SCHED_HEURISTIC && seg_flavour >= 0) D.flags |= trimk::F_LIVE_EDGES;
   // a fixed variant runs on its lean single-variant flavour
   int flavour = kFlavourAll;
-  if (variant <= TRIM_AC3_PULL) flavour = (int)variant;
+  if (inout) flavour = kFlavourInout;
+  else if (variant <= TRIM_AC3_PULL) flavour = (int)variant;
   else if (seg_flavour >= 0) flavour = seg_flavour;
   c->last_dev = D;
   const int grid = c->grids[flavour];
@@ -847,6 +874,13 @@ trim_err_t trim_run(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats
   if (variant >= TRIM_SCHED_HEURISTIC && variant <= TRIM_SCHED_SCRIPTED)
     return run_segmented(c, variant, stats);
   TRY(enqueue_run(c, variant));
+  return finish_run(c, stats);
+}
+
+trim_err_t trim_run_inout(trim_ctx* c, trim_run_stats_t* stats) {
+  if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  c->last_segments = 1;
+  TRY(enqueue_run(c, TRIM_AC4_PUSH, -1, 0, true));
   return finish_run(c, stats);
 }
 

@@ -130,6 +130,12 @@ struct Dev {
   uint32_t* w4_row;
   uint32_t* w4_eoff;
   uint32_t* chunk_first;  // [c]: work-list entry that owns edge 32c of the prefix
+  // in+out trimming (trim_run_inout): in-degree counters, and per work-list
+  // entry the vertex's out-CSR row start and in-degree (its edge range covers
+  // its G^T row, then its G row)
+  uint32_t* cnt_in;
+  uint32_t* w4_orow;
+  uint32_t* w4_din;
   uint32_t* bsum;     // per-CTA scratch of the grid-wide scan
   uint32_t sbuf_cap;  // entries of each CTA append buffer (dynamic shared memory)
   uint32_t resume;    // 1: continue the run from Ctrl::saved instead of starting it
@@ -220,6 +226,7 @@ __global__ void trim_persistent_kernel_m9(trimk::Dev D);   // AC-4 + schedulers 
 __global__ void trim_persistent_kernel_m10(trimk::Dev D);  // AC-6 + schedulers (segments)
 __global__ void trim_persistent_kernel_m12(trimk::Dev D);  // AC-3 + schedulers (segments)
 __global__ void trim_persistent_kernel_m15(trimk::Dev D);  // all variants + schedulers
+__global__ void trim_persistent_kernel_m17(trimk::Dev D);  // in+out trimming (AC-4 pushes on G and G^T)
 __global__ void trim_reset_ctrl_kernel(trimk::Ctrl* C);
 __global__ void trim_status_kernel(const uint32_t* level, uint32_t n, uint8_t* status);
 __global__ void trim_indeg_kernel(const uint32_t* tgt, uint64_t m, uint32_t n, uint32_t* cnt,

@@ -38,8 +38,9 @@
 
 // This file is compiled once per kernel flavour: TRIM_MODES is a bit set of the
 // variants the kernel can run (1 AC-4, 2 AC-6, 4 AC-3) plus 8 for the
-// per-round schedulers (features, heuristic, MLP, scripted lists). A fixed
-// variant gets a kernel with only its own path, hence fewer registers.
+// per-round schedulers (features, heuristic, MLP, scripted lists), or 17 for
+// in+out trimming. A fixed variant gets a kernel with only its own path,
+// hence fewer registers.
 #ifndef TRIM_MODES
 #define TRIM_MODES 15
 #endif
@@ -64,6 +65,9 @@ constexpr int MODES = TRIM_MODES;
 #define ROUND_FN __forceinline__
 #endif
 constexpr int M_AC4 = 1, M_AC6 = 2, M_AC3 = 4, M_SCHED = 8;
+// in+out trimming: AC-4 pushes on both G^T (out-degree counters) and G
+// (in-degree counters); its own flavour, with no other variant
+constexpr int M_INOUT = 16;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int MAX_WARPS = 16;   // blockDim.x <= 512
 constexpr int WBUF = 64;        // per-warp staging of supporting-set members
@@ -217,6 +221,10 @@ __device__ __forceinline__ void copy_slices(const Dev& D, const Cta& B, const Wa
       ee = w.edge_base + (i + 1 < w.nw4 ? se[i + 1] : w.nedge);
       D.w4_row[w.w4_base + i] = sr[i];
       D.w4_eoff[w.w4_base + i] = eo;
+      if (MODES & M_INOUT) {  // in+out entries: in-degree in slice 0, G row in slice 3
+        D.w4_din[w.w4_base + i] = sl[i];
+        D.w4_orow[w.w4_base + i] = sv[i];
+      }
     }
     mark_chunks(D, has, w.w4_base + i, eo, ee);
   }
@@ -330,6 +338,58 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   }
   __syncwarp();
 }
+
+#if TRIM_MODES & 16
+// Warp-collective, in+out trimming: lanes with pred were removed in round r
+// (their level is already set). Each joins the work list with one entry whose
+// edge range covers its G^T row (row, din edges: the predecessors whose
+// out-degree counters it decrements) and then its G row (orow, dout edges: the
+// successors whose in-degree counters it decrements). Removals are only
+// counted in the dead log, never written: no variant of this flavour reads it.
+__device__ __forceinline__ void append_dead_io(const Dev& D, Cta& B, bool pred, uint32_t u,
+                                               uint32_t r, bool pre, uint32_t prow,
+                                               uint32_t pdin, uint32_t porow, uint32_t pdout) {
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned mask = __ballot_sync(FULL, pred);
+  if (mask == 0u) return;
+  uint32_t row = 0, din = 0, orow = 0, dout = 0;
+  if (pred) {
+    if (pre) {
+      row = prow; din = pdin; orow = porow; dout = pdout;
+    } else {
+      row = __ldg(&D.ioff[u]);
+      din = __ldg(&D.ioff[u + 1]) - row;
+      orow = __ldg(&D.off[u]);
+      dout = __ldg(&D.off[u + 1]) - orow;
+    }
+  }
+  const bool w = pred && din + dout > 0u;
+  const unsigned wmask = __ballot_sync(FULL, w);
+  const unsigned k = __popc(mask), kw = __popc(wmask);
+  const unsigned ew = w ? din + dout : 0u;
+  const unsigned eincl = warp_incl_scan(ew);
+  const unsigned esum = __shfl_sync(FULL, eincl, 31);
+  WarpSlice& ws = B.ws[warp];
+  if (ws.nw4 + kw > w4_cap(B)) warp_flush(D, B, r, D.live0);
+  const uint32_t pw = ws.nw4, pe = ws.nedge;
+  const unsigned mdin = __reduce_max_sync(FULL, ew);
+  if (w) {
+    const unsigned at = pw + __popc(wmask & ((1u << lane) - 1u));
+    w4_rows(B, warp)[at] = row;
+    slice(warp, 2)[at] = pe + eincl - ew;
+    slice(warp, 0)[at] = din;
+    slice(warp, 3)[at] = orow;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    ws.ncount += k;
+    ws.nw4 = pw + kw;
+    ws.nedge = pe + esum;
+    ws.max_din = max(ws.max_din, mdin);
+  }
+  __syncwarp();
+}
+#endif
 
 // Warp-collective append of survivors to the AC-3 output live list.
 __device__ __forceinline__ void append_live(const Dev& D, Cta& B, bool pred, uint32_t v,
@@ -1162,6 +1222,70 @@ __device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
 }
 #endif
 
+#if TRIM_MODES & 16
+// ------------------------------------------------------------------ in+out
+
+// In+out round r (Section 4's remark: with G^T loaded a vertex also needs a
+// live incoming edge): every vertex removed before round r and not yet pushed
+// decrements the out-degree counter of each predecessor (its G^T row) and the
+// in-degree counter of each successor (its G row). A counter that reaches zero
+// removes its vertex in round r unless the vertex is already removed; when
+// both of a vertex's counters reach zero in the same round, the first
+// compare-and-swap of its level wins. Edges are balanced over the warps in
+// 32-edge chunks as in ac4_round.
+__device__ ROUND_FN void inout_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp,
+                                     uint32_t nwarps) {
+  constexpr int U = 4;
+  Counters K;
+  const unsigned lane = lane_id();
+  const uint32_t r = S.round;
+  const uint32_t ea = S.e_c4, eb = S.e_end, ia = S.c4w, ib = S.w_end;
+  if (eb <= ea) return;
+  const uint32_t c0 = ea >> 5, c1 = (eb + 31u) >> 5;
+  const uint32_t per = (c1 - c0 + nwarps - 1) / nwarps;
+  const uint32_t cb = c0 + gwarp * per, ce = min(c1, cb + per);
+  uint32_t cfb = 0;
+  for (uint32_t c = cb; c < ce; c += U) {
+    const uint32_t k = (c - cb) & 31u;
+    if (k == 0u) cfb = (c + lane < ce) ? ldcg(&D.chunk_first[c + lane]) : 0u;
+    uint32_t wrow[U], weo[U], worow[U], wdin[U], u[U], old[U];
+    bool valid[U], pred_in[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const uint32_t first = max(__shfl_sync(FULL, cfb, (k + q) & 31u), ia);
+      const uint32_t ii = first + lane;
+      const bool in = c + q < ce && ii < ib;
+      wrow[q] = in ? ldcg(&D.w4_row[ii]) : 0u;
+      weo[q] = in ? ldcg(&D.w4_eoff[ii]) : 0xFFFFFFFFu;
+      worow[q] = in ? ldcg(&D.w4_orow[ii]) : 0u;
+      wdin[q] = in ? ldcg(&D.w4_din[ii]) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const uint32_t e = ((c + q) << 5) + lane;
+      valid[q] = c + q < ce && e >= ea && e < eb;
+      const unsigned j = owner_of(weo[q], e);
+      const uint32_t kk = e - __shfl_sync(FULL, weo[q], j);
+      const uint32_t dj = __shfl_sync(FULL, wdin[q], j);
+      const uint32_t rj = __shfl_sync(FULL, wrow[q], j), oj = __shfl_sync(FULL, worow[q], j);
+      pred_in[q] = kk < dj;  // the edge lies in the entry's G^T row
+      u[q] = !valid[q] ? 0u : pred_in[q] ? __ldg(&D.itgt[rj + kk]) : __ldg(&D.tgt[oj + (kk - dj)]);
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q)
+      old[q] = valid[q] ? atomicSub(pred_in[q] ? &D.cnt[u[q]] : &D.cnt_in[u[q]], 1u) : 0u;
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      K.pushed += (valid[q] && pred_in[q]) ? 1 : 0;
+      K.edges += (valid[q] && !pred_in[q]) ? 1 : 0;
+      const bool pred = valid[q] && old[q] == 1u && atomicCAS(&D.level[u[q]], LIVE, r) == LIVE;
+      append_dead_io(D, B, pred, u[q], r, false, 0u, 0u, 0u, 0u);
+    }
+  }
+  stats_flush(D, B, K);
+}
+#endif
+
 // ------------------------------------------------------------------ AC-3
 
 __device__ ROUND_FN void ac3_round(const Dev& D, Cta& B, const Sched& S, uint32_t gwarp,
@@ -1435,12 +1559,23 @@ __device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32
       const uint32_t v = base + q * 32u + lane;
       const bool has = v < n;
       const uint32_t d = o1[q] - o0[q];
+#if TRIM_MODES & 16
+      // in+out: no out-edge or no in-edge removes the vertex in round 0
+      const uint32_t din = i1[q] - i0[q];
+      if (has) {
+        D.level[v] = (d && din) ? LIVE : 0u;
+        D.cnt[v] = d;
+        D.cnt_in[v] = din;
+      }
+      append_dead_io(D, B, has && (d == 0u || din == 0u), v, 0u, true, i0[q], din, o0[q], d);
+#else
       if (has) {
         D.level[v] = d ? LIVE : 0u;
         if (w4) D.cnt[v] = d;
         if (w6) D.supp[v] = 0u;
       }
       append_dead(D, B, has && d == 0u, v, 0u, D.live0, true, true, i0[q], i1[q] - i0[q]);
+#endif
     }
   }
 }
@@ -1510,7 +1645,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
   bool ok = true;
   if (!D.resume) {
     start_round(D, 0);
-    if (threadIdx.x == 0) B.w4_wide = 1;
+    if (threadIdx.x == 0) B.w4_wide = (MODES & M_INOUT) ? 0u : 1u;
     __syncthreads();
     init_round(D, B, gwarp, nwarps);
     flush_round(D, B, 0, D.live0);
@@ -1559,6 +1694,9 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     }
 #endif
     start_round(D, S.round);
+#if TRIM_MODES & 16
+    inout_round(D, B, S, gwarp, nwarps);
+#else
     if ((MODES & M_AC4) && S.variant == TRIM_AC4_PUSH) {
       ac4_round(D, B, S, gwarp, nwarps);
     } else if ((MODES & M_AC6) && S.variant == TRIM_AC6_SUPPORT) {
@@ -1566,6 +1704,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     } else if (MODES & M_AC3) {
       ac3_round(D, B, S, gwarp, nwarps);
     }
+#endif
     const bool stamp = (D.flags & F_ROUND_LOG) && blockIdx.x == 0 && threadIdx.x == 0;
     if (stamp) D.C->t_work[S.round & 3] = globaltimer();
     flush_round(D, B, S.round, S.live_out ? D.live1 : D.live0);
