@@ -19,6 +19,7 @@ import threading
 import numpy as np
 
 LIVE = 0xFFFFFFFF
+MASKED = 0xFFFFFFFE
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
@@ -55,6 +56,8 @@ def _L():
             lib.or_ac3.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u8p]
             lib.or_certificate.restype = ctypes.c_int64
             lib.or_certificate.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u8p]
+            lib.or_peel_masked.restype = ctypes.c_uint32
+            lib.or_peel_masked.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u8p, u32p, u8p]
             lib.or_peel_inout.restype = ctypes.c_uint32
             lib.or_peel_inout.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u32p, u32p, u8p]
             lib.or_certificate_inout.restype = ctypes.c_int64
@@ -154,3 +157,20 @@ def certificate_inout(off, tgt, level, status, csr_in=None) -> int:
     level = np.ascontiguousarray(level, np.uint32)
     status = np.ascontiguousarray(status, np.uint8)
     return int(_L().or_certificate_inout(n, off, tgt, off_in, tgt_in, level, status))
+
+
+def peel_masked(off, tgt, mask, csr_in=None):
+    """Trimming with the vertices where mask != 0 DEAD from the start (Section
+    9's vertex sampling; see or_peel_masked). Their level is MASKED; alpha
+    counts the steps that removed something. Returns (level, status, alpha)."""
+    off, tgt = _csr(off, tgt)
+    n = off.shape[0] - 1
+    off_in, tgt_in = transpose(off, tgt) if csr_in is None else csr_in
+    off_in, tgt_in = _csr(off_in, tgt_in)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    if mask.size == 0:
+        mask = np.zeros(1, np.uint8)
+    level = np.empty(max(n, 1), np.uint32)
+    status = np.empty(max(n, 1), np.uint8)
+    alpha = _L().or_peel_masked(n, off, off_in, tgt_in, mask, level, status)
+    return level[:n], status[:n], int(alpha)

@@ -28,6 +28,8 @@
  *                  AC-3 with G^T loaded): removal on no live successor OR no
  *                  live predecessor, one peeling step at a time
  *   or_certificate_inout  its local conditions (exactly one assignment)
+ *   or_peel_masked vertex-sampled inputs (Section 9, scalability experiment):
+ *                  unsampled vertices are DEAD from the start
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -305,4 +307,50 @@ int64_t or_certificate_inout(uint32_t n, const uint32_t* off, const uint32_t* tg
     }
   }
   return -1;
+}
+
+/* Vertex-sampled inputs. Section 9's scalability experiment samples vertices by
+ * setting the unsampled ones DEAD before trimming (and notes that AC-4 still
+ * computes their out-degree counters). Here mask[v] != 0 marks an unsampled
+ * vertex: it is DEAD from the start and gets level MASKED = 0xFFFFFFFE; it is
+ * not removed by any step and not counted in alpha. As in or_peel, counters
+ * start at |v.post|; the unsampled vertices first decrement the counter of each
+ * of their predecessors (they are dead before step 0), then step 0 removes
+ * every sampled vertex whose counter is zero, and the layer-synchronous
+ * peeling goes on from there. Returns alpha. */
+uint32_t or_peel_masked(uint32_t n, const uint32_t* off, const uint32_t* off_in,
+                        const uint32_t* tgt_in, const uint8_t* mask, uint32_t* level,
+                        uint8_t* status) {
+  const uint32_t MASKED = 0xFFFFFFFEu;
+  uint32_t* cnt = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4);
+  uint32_t* cur = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4);
+  uint32_t* nxt = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4);
+  uint32_t ncur = 0, alpha = 0;
+  for (uint32_t v = 0; v < n; ++v) {
+    cnt[v] = off[v + 1] - off[v];
+    level[v] = mask[v] ? MASKED : LIVE;
+  }
+  for (uint32_t w = 0; w < n; ++w) {  /* the unsampled vertices are dead before step 0 */
+    if (!mask[w]) continue;
+    for (uint32_t e = off_in[w]; e < off_in[w + 1]; ++e) cnt[tgt_in[e]] -= 1;
+  }
+  for (uint32_t v = 0; v < n; ++v)
+    if (!mask[v] && cnt[v] == 0) { level[v] = 0; cur[ncur++] = v; }
+  for (uint32_t r = 1; ncur > 0; ++r) {
+    alpha = r;
+    uint32_t nnxt = 0;
+    for (uint32_t i = 0; i < ncur; ++i) {
+      uint32_t w = cur[i];
+      for (uint32_t e = off_in[w]; e < off_in[w + 1]; ++e) {
+        uint32_t u = tgt_in[e];
+        if (mask[u]) continue;
+        cnt[u] -= 1;
+        if (cnt[u] == 0) { level[u] = r; nxt[nnxt++] = u; }
+      }
+    }
+    uint32_t* t = cur; cur = nxt; nxt = t; ncur = nnxt;
+  }
+  for (uint32_t v = 0; v < n; ++v) status[v] = (level[v] == LIVE);
+  free(cnt); free(cur); free(nxt);
+  return alpha;
 }
