@@ -490,6 +490,26 @@ def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None, mapped=Tru
     return g.m / statistics.mean(ts), copied, out.numel() * 4
 
 
+def vertex_sampling(P, t, g, flush, ratios=(0.1, 0.3, 0.5, 0.7, 0.9, 1.0), steps=10):
+    """Section 9's scalability experiment on this graph: a share `ratio` of
+    the vertices is sampled (a fixed uniform draw per vertex), the others are
+    DEAD from the start (trim_set_dead_mask); each fixed variant is timed."""
+    u = np.random.default_rng(2024).random(g.n)
+    out = {}
+    for ratio in ratios:
+        t.set_dead_mask((u >= ratio).astype(np.uint8))
+        row = {"sampled_vertices": int((u < ratio).sum())}
+        for v in ("ac4", "ac6", "ac3"):
+            ts, ks, st = time_variant(P, t, v, steps, 1, flush)
+            row[v] = {"ms": statistics.mean(ts), "rounds": st["rounds"], "trimmed": st["n_dead"]}
+        out[f"{ratio:.1f}"] = row
+        print(f"# sampled {ratio:.1f}: " + "  ".join(f"{v} {row[v]['ms']:.4f} ms"
+                                                   for v in ("ac4", "ac6", "ac3"))
+              + f"  trimmed {row['ac4']['trimmed']}", file=sys.stderr, flush=True)
+    t.set_dead_mask(None)
+    return out
+
+
 def extra_workload(P, idx, args, flush, stream, model):
     """A second workload timed in the same run (all its schedules; for the
     batched workload also each graph trimmed alone), as a sub-object of the
@@ -503,13 +523,18 @@ def extra_workload(P, idx, args, flush, stream, model):
     gofs = g.graph_off if batched else None
     names = ["ac4", "ac6", "ac3", "heuristic"] + (["learned"] if model is not None else []) \
         + ([] if batched else ["inout"])
+    sampling = None
     with P.Trimmer(*bufs, stream=stream) as t:
         if model is not None:
             t.set_model(model)
         sweep = sweep_variants(P, t, g, args, tuned_key(idx, False), names, flush, gofs,
                                label=f"[{idx}] ")
+        if idx == 1:
+            sampling = vertex_sampling(P, t, g, flush)
     out = {"workload": wname, "n": g.n, "m": g.m, "variants": sweep,
            "schedules": schedules_summary(sweep)}
+    if sampling:
+        out["vertex_sampling"] = sampling
     if batched:
         out["graphs"] = int(len(g.graph_off) - 1)
         out["timing"] = ("CUDA events around trim_batch_run: one replayed CUDA graph "

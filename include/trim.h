@@ -36,6 +36,7 @@ extern "C" {
 #endif
 
 #define TRIM_LIVE 0xFFFFFFFFu
+#define TRIM_MASKED 0xFFFFFFFEu /* trim_level of a vertex set DEAD by trim_set_dead_mask */
 
 typedef enum {
   TRIM_OK = 0,
@@ -187,6 +188,18 @@ trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void
  * that trim_run_async uses. */
 trim_err_t trim_run(trim_ctx* ctx, trim_variant_t variant, trim_run_stats_t* stats);
 
+/* Vertex sampling (Section 9's scalability experiment samples vertices by setting
+ * the unsampled ones DEAD before trimming). mask: n bytes, mask[v] != 0 makes v
+ * DEAD from the start (status 0, level TRIM_MASKED); on the device if on_device
+ * (device memory of the context's GPU), else on the host; copied, so the caller
+ * may free it at once. NULL clears the mask. The mask applies to every later
+ * trim_run, trim_run_async and trim_batch_run (any variant or schedule) until it
+ * is changed; the result equals trimming the subgraph induced by the unmasked
+ * vertices. rounds and n_dead of the run statistics count only vertices removed
+ * by trimming. trim_run_inout refuses to run while a mask is set
+ * (TRIM_ERR_INVALID_ARG). */
+trim_err_t trim_set_dead_mask(trim_ctx* ctx, const uint8_t* mask, int on_device);
+
 /* In+out trimming: removes every vertex that has no live successor OR no live
  * predecessor, repeatedly (Section 4's remark on checking the in-degree when
  * the transposed graph is in memory; Section 1: the size-1 SCC trimming that
@@ -220,7 +233,8 @@ trim_err_t trim_status(const trim_ctx* ctx, uint8_t* out, int out_on_device);
 
 /* Output of the last run: out[v] = the peeling step that removed v (0 for a vertex
  * without out-edges; else 1 + the largest level among its successors, i.e. the
- * length of its longest path to a sink), or TRIM_LIVE. n uint32 values. */
+ * length of its longest path to a sink), TRIM_LIVE, or TRIM_MASKED for a vertex
+ * the dead mask set DEAD. n uint32 values. */
 trim_err_t trim_level(const trim_ctx* ctx, uint32_t* out, int out_on_device);
 
 /* Device pointer to the context's level array (n uint32, valid until the next

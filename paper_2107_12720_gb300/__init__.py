@@ -15,7 +15,7 @@ import os
 
 import numpy as np
 
-from .abi import (LIB_PATH, TRIM_AC3_PULL, TRIM_AC4_PUSH, TRIM_AC6_SUPPORT, TRIM_FLAG_ROUND_LOG,
+from .abi import (LIB_PATH, TRIM_MASKED, TRIM_AC3_PULL, TRIM_AC4_PUSH, TRIM_AC6_SUPPORT, TRIM_FLAG_ROUND_LOG,
                   TRIM_FLAG_STATS, TRIM_FLAG_VALIDATE, TRIM_LIVE, TRIM_MEM_DEVICE, TRIM_MEM_HOST,
                   TRIM_MEM_HOST_MAPPED, TRIM_MLP_NBLOB,
                   TRIM_MLP_NPARAMS, TRIM_SCHED_HEURISTIC, TRIM_SCHED_LEARNED,
@@ -25,7 +25,7 @@ from .abi import (trim_batch_run, trim_create, trim_default_params, trim_destroy
                   trim_get_params, trim_get_round_log, trim_last_error, trim_level,
                   trim_level_device_ptr, trim_mlp_adam_step, trim_mlp_forward, trim_mlp_loss_grad,
                   trim_mlp_scratch_bytes, trim_run, trim_run_async, trim_run_inout,
-                  trim_set_alloc_limit,
+                  trim_set_alloc_limit, trim_set_dead_mask,
                   trim_set_model, trim_set_params, trim_set_schedule, trim_status, trim_sync)
 
 VARIANTS = {"ac4": TRIM_AC4_PUSH, "ac6": TRIM_AC6_SUPPORT, "ac3": TRIM_AC3_PULL,
@@ -99,6 +99,25 @@ class Trimmer:
 
     def run(self, variant="ac4") -> dict:
         return _stats_dict(trim_run(self.ctx, _variant(variant)))
+
+    def set_dead_mask(self, mask) -> None:
+        """Vertices with mask != 0 are DEAD from the start of every later run
+        (vertex sampling); None clears the mask. numpy / CPU tensor: host,
+        CUDA tensor: device (copied either way)."""
+        import torch
+        if mask is None:
+            trim_set_dead_mask(self.ctx, None, 0)
+            return
+        if isinstance(mask, torch.Tensor) and mask.is_cuda:
+            if mask.numel() != self.n:
+                raise TrimError(1, "mask must have n entries")
+            m = (mask != 0).to(torch.uint8).contiguous()
+            trim_set_dead_mask(self.ctx, m.data_ptr(), 1)
+            return
+        m = np.ascontiguousarray(np.asarray(mask) != 0, np.uint8)
+        if m.shape[0] != self.n:
+            raise TrimError(1, "mask must have n entries")
+        trim_set_dead_mask(self.ctx, m.ctypes.data, 0)
 
     def run_inout(self) -> dict:
         """In+out trimming (no live successor or no live predecessor removes a

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtrim.so")
 
 TRIM_LIVE = 0xFFFFFFFF
+TRIM_MASKED = 0xFFFFFFFE
 TRIM_AC4_PUSH, TRIM_AC6_SUPPORT, TRIM_AC3_PULL = 0, 1, 2
 TRIM_SCHED_HEURISTIC, TRIM_SCHED_LEARNED, TRIM_SCHED_SCRIPTED = 3, 4, 5
 TRIM_FLAG_VALIDATE, TRIM_FLAG_STATS, TRIM_FLAG_ROUND_LOG = 1, 2, 4
@@ -68,6 +69,7 @@ SIGNATURES = [
                          ctypes.POINTER(_P)]),
     ("trim_run", _I, [_P, _I, ctypes.POINTER(TrimRunStats)]),
     ("trim_run_inout", _I, [_P, ctypes.POINTER(TrimRunStats)]),
+    ("trim_set_dead_mask", _I, [_P, _P, _I]),
     ("trim_run_async", _I, [_P, _I]),
     ("trim_sync", _I, [_P, ctypes.POINTER(TrimRunStats)]),
     ("trim_status", _I, [_P, _P, _I]),
@@ -145,6 +147,10 @@ def trim_run_inout(ctx) -> TrimRunStats:
     s = TrimRunStats()
     check(lib().trim_run_inout(ctx, ctypes.byref(s)), ctx)
     return s
+
+
+def trim_set_dead_mask(ctx, mask, on_device: int) -> None:
+    check(lib().trim_set_dead_mask(ctx, _ptr(mask), on_device), ctx)
 
 
 def trim_run_async(ctx, variant: int) -> None:

@@ -44,6 +44,8 @@ struct trim_ctx {
   // in+out runs: in-degree counters, the work list's G rows and in-degrees, and
   // the chunk-owner index of its edge space (both rows: up to 2m edges)
   uint32_t *cnt_in = nullptr, *w4_orow = nullptr, *w4_din = nullptr, *chunk_io = nullptr;
+  uint8_t* mask = nullptr;  // trim_set_dead_mask: device copy of the dead mask
+  bool has_mask = false;
   Ctrl* ctrl = nullptr;
   Ctrl* h_ctrl = nullptr;  // host mirror of the control block for read-back
   bool h_ctrl_pinned = false;
@@ -563,6 +565,7 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   if ((int)variant < 0 || variant > TRIM_SCHED_SCRIPTED)
     return fail(c, TRIM_ERR_INVALID_ARG, "unknown variant");
   if (inout) {
+    if (c->has_mask) return fail(c, TRIM_ERR_INVALID_ARG, "trim_run_inout does not take a dead mask");
     if (c->ioff == nullptr) TRY(build_transpose(c));
     TRY(ensure_inout(c));
   }
@@ -617,6 +620,7 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   D.live1 = c->live1; D.w4_row = c->w4_row; D.w4_eoff = c->w4_eoff;
   D.chunk_first = c->chunk_first; D.bsum = c->bsum; D.C = c->ctrl;
   D.cnt_in = c->cnt_in; D.w4_orow = c->w4_orow; D.w4_din = c->w4_din;
+  D.mask = c->has_mask ? c->mask : nullptr;
   if (inout) D.chunk_first = c->chunk_io;
   D.sbuf_cap = kSbufCap;
   D.rlog = c->rlog; D.rlog_cap = c->rlog_cap;
@@ -746,6 +750,11 @@ trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read) {
       return fail(c, (trim_err_t)h.err,
                   "device reported error " + std::to_string(h.err) + " (info " +
                       std::to_string(h.err_info) + ")");
+    }
+    if (c->has_mask && c->n) {  // masked vertices report TRIM_MASKED (level 0 inside the run)
+      trim_mask_levels_kernel<<<c->sm_count * 4, 512, 0, c->stream>>>(c->level, c->mask, c->n);
+      CK(cudaGetLastError());
+      TRY(sync_check(c));
     }
     trim_run_stats_t s{};
     s.rounds = h.rounds;
@@ -1006,6 +1015,23 @@ trim_err_t trim_set_model(trim_ctx* c, const float* blob, size_t n_floats) {
   CK(cudaMemcpyAsync(c->model, blob, TRIM_MLP_NBLOB * 4, cudaMemcpyHostToDevice, c->stream));
   TRY(sync_check(c));
   c->has_model = true;
+  return TRIM_OK;
+}
+
+trim_err_t trim_set_dead_mask(trim_ctx* c, const uint8_t* mask, int on_device) {
+  if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  if (c->pending) TRY(finish_run(c, nullptr));
+  drop_batch_graph(c);
+  if (mask == nullptr) {
+    c->has_mask = false;
+    return TRIM_OK;
+  }
+  if (c->n && !c->mask) TRY(dalloc(c, &c->mask, c->n));
+  if (c->n)
+    CK(cudaMemcpyAsync(c->mask, mask, c->n,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  TRY(sync_check(c));
+  c->has_mask = true;
   return TRIM_OK;
 }
 

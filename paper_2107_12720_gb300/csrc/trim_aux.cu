@@ -60,6 +60,14 @@ __global__ void trim_status_kernel(const uint32_t* level, uint32_t n, uint8_t* s
     status[v] = level[v] == LIVE ? 1 : 0;
 }
 
+// After a run with a dead mask: masked vertices carry level 0 inside the run
+// (removed before round 1, so every variant's "level[u] < r" test skips them);
+// their reported level is TRIM_MASKED.
+__global__ void trim_mask_levels_kernel(uint32_t* level, const uint8_t* mask, uint32_t n) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (mask[v]) level[v] = TRIM_MASKED;
+}
+
 // in-degree histogram of the targets (and a check that every target is < n)
 __global__ void trim_indeg_kernel(const uint32_t* tgt, uint64_t m, uint32_t n, uint32_t* cnt,
                                   uint32_t* bad) {

@@ -136,6 +136,9 @@ struct Dev {
   uint32_t* cnt_in;
   uint32_t* w4_orow;
   uint32_t* w4_din;
+  // vertex sampling (trim_set_dead_mask): mask[v] != 0 marks a vertex that is
+  // DEAD from the start; nullable
+  const uint8_t* __restrict__ mask;
   uint32_t* bsum;     // per-CTA scratch of the grid-wide scan
   uint32_t sbuf_cap;  // entries of each CTA append buffer (dynamic shared memory)
   uint32_t resume;    // 1: continue the run from Ctrl::saved instead of starting it
@@ -229,6 +232,7 @@ __global__ void trim_persistent_kernel_m15(trimk::Dev D);  // all variants + sch
 __global__ void trim_persistent_kernel_m17(trimk::Dev D);  // in+out trimming (AC-4 pushes on G and G^T)
 __global__ void trim_reset_ctrl_kernel(trimk::Ctrl* C);
 __global__ void trim_status_kernel(const uint32_t* level, uint32_t n, uint8_t* status);
+__global__ void trim_mask_levels_kernel(uint32_t* level, const uint8_t* mask, uint32_t n);
 __global__ void trim_indeg_kernel(const uint32_t* tgt, uint64_t m, uint32_t n, uint32_t* cnt,
                                   uint32_t* bad);
 __global__ void trim_scan_blocks_kernel(const uint32_t* in, uint32_t n, uint32_t* out,

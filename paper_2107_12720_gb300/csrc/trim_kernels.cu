@@ -1580,6 +1580,63 @@ __device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32
   }
 }
 
+#if !(TRIM_MODES & 16)
+// Initial pass with a dead mask (vertex sampling, Section 9): a masked vertex
+// is DEAD from the start: level 0 (removed before round 1 for every variant),
+// counter 0 (a decrement can never return 1), never on the work list, not
+// counted. An unmasked vertex counts its unmasked successors: with none it is
+// removed in round 0, else it is LIVE with that count as its AC-4 counter. A
+// run without AC-4 needs no count, only whether one unmasked successor exists,
+// so its scans stop at the first one. One lane per vertex; rows longer than 32
+// are scanned by the whole warp.
+__device__ ROUND_FN void init_round_masked(const Dev& D, Cta& B, uint32_t gwarp,
+                                           uint32_t nwarps) {
+  const unsigned lane = lane_id();
+  const uint32_t n = D.n;
+  const bool w4 = (D.flags & F_AC4_POSSIBLE) != 0;
+  const bool w6 = (D.flags & (F_AC6_POSSIBLE | F_AC3_POSSIBLE)) != 0;
+  const bool rows = D.ioff != nullptr;
+  for (uint32_t base = gwarp * 32u; base < n; base += nwarps * 32u) {
+    const uint32_t v = base + lane;
+    const bool has = v < n;
+    const bool masked = has && D.mask[v] != 0;
+    const uint32_t s = has ? __ldg(&D.off[v]) : 0u;
+    const uint32_t d = has ? __ldg(&D.off[v + 1]) - s : 0u;
+    const uint32_t i0 = (has && rows) ? __ldg(&D.ioff[v]) : 0u;
+    const uint32_t i1 = (has && rows) ? __ldg(&D.ioff[v + 1]) : 0u;
+    const bool own = has && !masked && d <= 32u;  // counted by its own lane
+    uint32_t c = 0;
+    for (uint32_t k0 = 0; k0 < (own ? d : 0u) && (w4 || c == 0u); k0 += 4u) {
+      uint32_t t[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[q] = (k0 + q < d) ? __ldg(&D.tgt[s + k0 + q]) : 0u;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c += (k0 + q < d && D.mask[t[q]] == 0) ? 1u : 0u;
+    }
+    unsigned big = __ballot_sync(FULL, has && !masked && d > 32u);
+    while (big) {
+      const int j = __ffs(big) - 1;
+      big &= big - 1u;
+      const uint32_t sj = __shfl_sync(FULL, s, j), dj = __shfl_sync(FULL, d, j);
+      uint32_t part = 0;
+      for (uint32_t k0 = 0; k0 < dj; k0 += 32u) {  // warp-uniform
+        const uint32_t k = k0 + lane;
+        part += (k < dj && D.mask[__ldg(&D.tgt[sj + k])] == 0) ? 1u : 0u;
+        if (!w4 && __any_sync(FULL, part != 0u)) break;
+      }
+      part = __reduce_add_sync(FULL, part);
+      if ((int)lane == j) c = part;
+    }
+    if (has) {
+      D.level[v] = (masked || c == 0u) ? 0u : LIVE;
+      if (w4) D.cnt[v] = masked ? 0u : c;
+      if (w6) D.supp[v] = 0u;
+    }
+    append_dead(D, B, has && !masked && c == 0u, v, 0u, D.live0, true, true, i0, i1 - i0);
+  }
+}
+#endif
+
 }  // namespace
 
 #ifndef TRIM_MIN_BLOCKS
@@ -1647,7 +1704,11 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     start_round(D, 0);
     if (threadIdx.x == 0) B.w4_wide = (MODES & M_INOUT) ? 0u : 1u;
     __syncthreads();
-    init_round(D, B, gwarp, nwarps);
+#if !(TRIM_MODES & 16)
+    if (D.mask != nullptr) init_round_masked(D, B, gwarp, nwarps);
+    else
+#endif
+      init_round(D, B, gwarp, nwarps);
     flush_round(D, B, 0, D.live0);
     ok = grid_barrier(D, B, false);
     // every warp's copy finished before the barrier; the __syncthreads after

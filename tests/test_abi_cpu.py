@@ -139,5 +139,5 @@ def test_header_constants_match_binding():
     hdr = open(os.path.join(ROOT, "include", "trim.h")).read()
     defs = dict(re.findall(r"#define (TRIM_[A-Z0-9_]+) \(?([0-9xA-Fa-f]+)u?", hdr))
     for name in ["TRIM_MEM_HOST", "TRIM_MEM_DEVICE", "TRIM_MEM_HOST_MAPPED", "TRIM_FLAG_VALIDATE",
-                 "TRIM_FLAG_STATS", "TRIM_FLAG_ROUND_LOG"]:
+                 "TRIM_FLAG_STATS", "TRIM_FLAG_ROUND_LOG", "TRIM_LIVE", "TRIM_MASKED"]:
         assert int(defs[name], 0) == getattr(abi, name), name
