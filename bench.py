@@ -490,6 +490,39 @@ def e2e_measure(P, g, off_in, tgt_in, variant, steps, graph_off=None, mapped=Tru
     return g.m / statistics.mean(ts), copied, out.numel() * 4
 
 
+def split_by_size(P, g, args, flush, stream, max_n=4096, max_m=65536, steps=20):
+    """Bound on what trimming the small graphs of a batch apart (one CTA each,
+    from a device-side queue) could save: the batched AC-4 time of the union
+    of only the graphs above one CTA's capacity (max_n vertices or max_m
+    edges), and of only the small ones, next to the whole union. Even if the
+    small graphs cost nothing elsewhere, a split saves at most
+    union - union_of_large_graphs."""
+    import torch
+    import graphgen
+    go = g.graph_off.astype(np.int64)
+    parts, small = [], []
+    for gi in range(len(go) - 1):
+        a, b = int(go[gi]), int(go[gi + 1])
+        off = (g.off[a:b + 1] - g.off[a]).astype(np.uint32)
+        tgt = (g.tgt[g.off[a]:g.off[b]] - a).astype(np.uint32)
+        parts.append(graphgen.Graph(off, tgt))
+        small.append((b - a) <= max_n and int(off[-1]) <= max_m)
+    out = {"max_n": max_n, "max_m": max_m, "small_graphs": int(sum(small)),
+           "small_edges_share": sum(p.m for p, s_ in zip(parts, small) if s_) / g.m}
+    for name, sel in (("union_of_large_graphs", [not x for x in small]),
+                      ("union_of_small_graphs", small)):
+        u = graphgen.union([p for p, s_ in zip(parts, sel) if s_])
+        oi, ti = host_transpose(u.off, u.tgt)
+        dev = lambda a: torch.from_numpy(a.view(np.int32)).cuda()
+        with P.Trimmer(dev(u.off), dev(u.tgt), dev(oi), dev(ti), stream=stream) as t:
+            apply_tuned(t, args, "ac4", tuned_key(3, False))
+            ts, ks, st = time_variant(P, t, "ac4", steps, 2, flush, u.graph_off)
+        out[name] = {"ms": statistics.mean(ts), "rounds": st["rounds"], "m": u.m}
+        print(f"# [3] {name}: {statistics.mean(ts):.4f} ms rounds {st['rounds']} m {u.m}",
+              file=sys.stderr, flush=True)
+    return out
+
+
 def vertex_sampling(P, t, g, flush, ratios=(0.1, 0.3, 0.5, 0.7, 0.9, 1.0), steps=10):
     """Section 9's scalability experiment on this graph: a share `ratio` of
     the vertices is sampled (a fixed uniform draw per vertex), the others are
@@ -541,6 +574,7 @@ def extra_workload(P, idx, args, flush, stream, model):
                          "(control-block reset + persistent kernel) for all graphs")
         ms, cnt = per_graph_fixed(P, g, "ac4", args.per_graph if args.per_graph > 0 else None)
         best = min(sweep[v]["ms"] for v in ("ac4", "ac6", "ac3"))
+        out["split_by_size"] = split_by_size(P, g, args, flush, stream)
         out["per_graph_fixed"] = {"schedule": "ac4, each graph trimmed alone (one launch each)",
                                   "ms": ms, "value": g.m / (ms * 1e-3), "unit": UNIT,
                                   "graphs_timed": cnt, "batched_speedup": ms / best}
