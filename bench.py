@@ -543,6 +543,43 @@ def vertex_sampling(P, t, g, flush, ratios=(0.1, 0.3, 0.5, 0.7, 0.9, 1.0), steps
     return out
 
 
+def implicit_comparison(P, flush, stream, steps=3):
+    """Section 2.1's on-the-fly property: the deep-cascade recipe (2^24
+    vertices, chains) as an implicit graph whose successors the AC-6 and AC-3
+    kernels compute, against the same graph stored as a CSR (configs index 2).
+    Reports time and edges inspected (the work counter) for each."""
+    import torch
+    import graphgen.configs as cfg
+    n = 1 << 24
+    nC, nR = n // 10, n // 5
+    spec = dict(seed=3, nC=nC, nR=nR, nT=n - nC - nR, c_k=(8, 8), r_k=(1, 15), t_k=(0, 14),
+                n_chains=4096)
+    out = {"workload": "deep_cascade recipe (2^24 vertices, 4,096 chains), seed 3: implicit "
+                       "(successors computed by the kernels) and stored as a CSR"}
+    g = cfg.config(2)
+    oi, ti = host_transpose(g.off, g.tgt)
+    dev = lambda a: torch.from_numpy(a.view(np.int32)).cuda()
+    for kind in ("implicit", "csr"):
+        make = (lambda flags=0: P.Trimmer.implicit(**spec, stream=stream, flags=flags)) \
+            if kind == "implicit" else \
+            (lambda flags=0: P.Trimmer(dev(g.off), dev(g.tgt), dev(oi), dev(ti), stream=stream,
+                                       flags=flags))
+        row = {}
+        for v in ("ac6", "ac3"):
+            with make(P.TRIM_FLAG_STATS) as t:
+                inspected = t.run(v)["edges_inspected"]
+            with make() as t:
+                ts, ks, st = time_variant(P, t, v, steps, 1, flush)
+            ms = statistics.mean(ts)
+            row[v] = {"ms": ms, "edges_inspected": int(inspected),
+                      "inspected_per_s": inspected / (ms * 1e-3), "rounds": st["rounds"]}
+            print(f"# {kind:8s} {v}: {ms:9.3f} ms  inspected {inspected:.3e}", file=sys.stderr,
+                  flush=True)
+        out[kind] = row
+    out["m_csr"] = g.m
+    return out
+
+
 def extra_workload(P, idx, args, flush, stream, model):
     """A second workload timed in the same run (all its schedules; for the
     batched workload also each graph trimmed alone), as a sub-object of the
@@ -678,6 +715,7 @@ def run_ours(args, rank, ws, local):
     if rank == 0 and args.extra and args.config == 4 and not args.small:
         for idx in (1, 3):
             extra[f"config{idx}"] = extra_workload(P, idx, args, flush, stream, model)
+        extra["implicit"] = implicit_comparison(P, flush, stream)
     if rank != 0:
         return
     peak, peak_kind = measured_peaks()

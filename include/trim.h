@@ -188,6 +188,47 @@ trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void
  * that trim_run_async uses. */
 trim_err_t trim_run(trim_ctx* ctx, trim_variant_t variant, trim_run_stats_t* stats);
 
+/* ---- Implicit graphs (Section 2.1, "On-the-fly Property") ----
+ * A graph given as G = (v0, POST): no CSR in memory, the successors of a vertex
+ * are computed when a kernel needs them. AC-6 and AC-3 only ever read
+ * successors, so they run on such a graph (AC-4 needs G^T and cannot; the
+ * paper's Table 1). The library's built-in family is a seeded planted graph:
+ * vertices C = [0, nC) (core), R = [nC, nC+nR) (reaching set) and
+ * T = [nC+nR, n) (trimmable, rank = v - nC - nR), n = nC + nR + nT. With
+ *   mix(z):    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27;
+ *              z *= 0x94D049BB133111EB; z ^= z >> 31     (SplitMix64)
+ *   key(v)   = mix(seed ^ mix(salt + v + 0x9E3779B97F4A7C15))
+ *   word(v,i)= mix(key(v) + (i + 1) * 0x9E3779B97F4A7C15)
+ *   below(w,k)= floor(w * k / 2^64)                         (Lemire)
+ *   draw(lo,hi) = lo + below(word(v, 0), hi - lo + 1)
+ * vertex v has degree k(v) and successors s_j(v), j < k(v), with w = word(v, 1+j):
+ *   v in C: k = draw(c_kmin, c_kmax),   s_j = below(w, nC)
+ *   v in R: k = draw(r_kmin, r_kmax),   s_0 = below(w, nC), s_j = below(w, nC + nR)
+ *   v in T, n_chains = 0: k = 0 if rank < t_sinks else draw(t_kmin, t_kmax);
+ *                         s_j = nC + nR + below(w, rank)
+ *   v in T, n_chains > 0 (chains, pos = rank / n_chains): k = 0 at pos 0, else
+ *                         1 + draw(t_kmin, t_kmax); s_0 = v - n_chains (the chain
+ *                         predecessor), s_j = nC + nR + below(w, pos * n_chains).
+ * Rows may repeat a successor; that changes no result. nR > 0 needs nC > 0. */
+typedef struct {
+  uint64_t seed;
+  uint64_t salt;
+  uint32_t nC, nR, nT;
+  uint32_t c_kmin, c_kmax;
+  uint32_t r_kmin, r_kmax;
+  uint32_t t_sinks, t_kmin, t_kmax;
+  uint32_t n_chains;
+} trim_implicit_graph_t;
+
+/* Creates a context over an implicit graph (no CSR is copied or stored: memory
+ * is O(n)). Only TRIM_AC6_SUPPORT and TRIM_AC3_PULL can run on it (trim_run,
+ * trim_run_async); every other call that needs edges in memory (other variants
+ * and schedules, trim_run_inout, trim_batch_run, a dead mask) fails with
+ * TRIM_ERR_INVALID_ARG. The edge count m (the sum of the degrees) is computed
+ * on the device here. flags: TRIM_FLAG_STATS, TRIM_FLAG_ROUND_LOG. */
+trim_err_t trim_create_implicit(const trim_implicit_graph_t* g, void* cuda_stream, uint32_t flags,
+                                trim_ctx** out);
+
 /* Vertex sampling (Section 9's scalability experiment samples vertices by setting
  * the unsampled ones DEAD before trimming). mask: n bytes, mask[v] != 0 makes v
  * DEAD from the start (status 0, level TRIM_MASKED); on the device if on_device

@@ -19,9 +19,11 @@ from .abi import (LIB_PATH, TRIM_MASKED, TRIM_AC3_PULL, TRIM_AC4_PUSH, TRIM_AC6_
                   TRIM_FLAG_STATS, TRIM_FLAG_VALIDATE, TRIM_LIVE, TRIM_MEM_DEVICE, TRIM_MEM_HOST,
                   TRIM_MEM_HOST_MAPPED, TRIM_MLP_NBLOB,
                   TRIM_MLP_NPARAMS, TRIM_SCHED_HEURISTIC, TRIM_SCHED_LEARNED,
-                  TRIM_SCHED_SCRIPTED, TrimCsr, TrimError, TrimParams, TrimRoundRec,
+                  TRIM_SCHED_SCRIPTED, TrimCsr, TrimError, TrimImplicitGraph, TrimParams,
+                  TrimRoundRec,
                   TrimRunStats, lib, check)
-from .abi import (trim_batch_run, trim_create, trim_default_params, trim_destroy,
+from .abi import (trim_batch_run, trim_create, trim_create_implicit, trim_default_params,
+                  trim_destroy,
                   trim_get_params, trim_get_round_log, trim_last_error, trim_level,
                   trim_level_device_ptr, trim_mlp_adam_step, trim_mlp_forward, trim_mlp_loss_grad,
                   trim_mlp_scratch_bytes, trim_run, trim_run_async, trim_run_inout,
@@ -76,6 +78,27 @@ class Trimmer:
         self.n = out_csr.n
         self.m = out_csr.m
         self.flags = flags
+
+    @classmethod
+    def implicit(cls, seed: int, nC: int, nR: int, nT: int, c_k=(4, 4), r_k=(1, 4), t_sinks=0,
+                 t_k=(1, 4), n_chains=0, salt: int = 0, stream=None, flags: int = 0):
+        """A context over the library's implicit planted graph (no CSR in
+        memory; successors computed on the fly, see trim_create_implicit).
+        Only run("ac6") and run("ac3") apply."""
+        import torch
+        self = cls.__new__(cls)
+        self._keep = []
+        g = TrimImplicitGraph(seed, salt, nC, nR, nT, c_k[0], c_k[1], r_k[0], r_k[1], t_sinks,
+                              t_k[0], t_k[1], n_chains)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+        self.ctx = trim_create_implicit(g, sp, flags)
+        self.n = nC + nR + nT
+        self.m = None
+        self.flags = flags
+        return self
 
     def _csr(self, off, tgt):
         import torch

@@ -45,6 +45,12 @@ class TrimParams(ctypes.Structure):
                 ("heur_ac6_ratio", ctypes.c_float), ("local_round_edges", ctypes.c_uint32)]
 
 
+class TrimImplicitGraph(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("salt", ctypes.c_uint64)] + [
+        (k, ctypes.c_uint32) for k in ("nC", "nR", "nT", "c_kmin", "c_kmax", "r_kmin", "r_kmax",
+                                       "t_sinks", "t_kmin", "t_kmax", "n_chains")]
+
+
 class TrimRunStats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint32), ("n_dead", ctypes.c_uint32),
                 ("device_ms", ctypes.c_float), ("edges_inspected", ctypes.c_uint64),
@@ -69,6 +75,8 @@ SIGNATURES = [
                          ctypes.POINTER(_P)]),
     ("trim_run", _I, [_P, _I, ctypes.POINTER(TrimRunStats)]),
     ("trim_run_inout", _I, [_P, ctypes.POINTER(TrimRunStats)]),
+    ("trim_create_implicit", _I, [ctypes.POINTER(TrimImplicitGraph), _P, _U32,
+                                  ctypes.POINTER(_P)]),
     ("trim_set_dead_mask", _I, [_P, _P, _I]),
     ("trim_run_async", _I, [_P, _I]),
     ("trim_sync", _I, [_P, ctypes.POINTER(TrimRunStats)]),
@@ -141,6 +149,12 @@ def trim_run(ctx, variant: int) -> TrimRunStats:
     s = TrimRunStats()
     check(lib().trim_run(ctx, variant, ctypes.byref(s)), ctx)
     return s
+
+
+def trim_create_implicit(graph: TrimImplicitGraph, stream, flags: int):
+    ctx = ctypes.c_void_p()
+    check(lib().trim_create_implicit(ctypes.byref(graph), stream, flags, ctypes.byref(ctx)), None)
+    return ctx
 
 
 def trim_run_inout(ctx) -> TrimRunStats:

@@ -26,6 +26,8 @@ UNITS = [("trim_kernels.cu", ["-DTRIM_MODES=1"], "trim_kernels_m1.o"),
          ("trim_kernels.cu", ["-DTRIM_MODES=12"], "trim_kernels_m12.o"),
          ("trim_kernels.cu", ["-DTRIM_MODES=15"], "trim_kernels_m15.o"),
          ("trim_kernels.cu", ["-DTRIM_MODES=17"], "trim_kernels_m17.o"),
+         ("trim_kernels.cu", ["-DTRIM_MODES=34"], "trim_kernels_m34.o"),
+         ("trim_kernels.cu", ["-DTRIM_MODES=36"], "trim_kernels_m36.o"),
          ("trim_aux.cu", [], "trim_aux.o"),
          ("trim_api.cu", [], "trim_api.o"),
          ("trim_noalloc.cu", [], "trim_noalloc.o"),

@@ -46,6 +46,8 @@ struct trim_ctx {
   uint32_t *cnt_in = nullptr, *w4_orow = nullptr, *w4_din = nullptr, *chunk_io = nullptr;
   uint8_t* mask = nullptr;  // trim_set_dead_mask: device copy of the dead mask
   bool has_mask = false;
+  bool implicit = false;      // trim_create_implicit: successors computed, no CSR
+  trim_implicit_graph_t ig{};
   Ctrl* ctrl = nullptr;
   Ctrl* h_ctrl = nullptr;  // host mirror of the control block for read-back
   bool h_ctrl_pinned = false;
@@ -57,7 +59,7 @@ struct trim_ctx {
   uint32_t script_len = 0;
   uint8_t* status_tmp = nullptr;
   trim_params_t params{};
-  int grids[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // cooperative grid size of each kernel flavour
+  int grids[10] = {};  // cooperative grid size of each kernel flavour
   trimk::Dev last_dev{};        // arguments of the last launch (segments reuse them)
   int seg_first[3] = {-1, -1, -1};  // per scheduled mode: flavour of its last first round
   uint64_t last_segments = 0;       // kernel launches of the last trim_run
@@ -249,16 +251,18 @@ size_t dyn_smem_bytes(uint32_t block_threads) {
 
 // kernel flavours: index 0..3 = AC-4 only, AC-6 only, AC-3 only, everything;
 // 4..6 = AC-4, AC-6, AC-3 each with the per-round schedulers (segments);
-// 7 = in+out trimming
+// 7 = in+out trimming; 8, 9 = AC-6, AC-3 on an implicit graph
 typedef void (*persistent_fn)(trimk::Dev);
-constexpr int kNumFlavours = 8;
+constexpr int kNumFlavours = 10;
 constexpr int kFlavourAll = 3;
 constexpr int kFlavourSeg = 4;  // + variant
 constexpr int kFlavourInout = 7;
+constexpr int kFlavourImplicitAC6 = 8, kFlavourImplicitAC3 = 9;
 const persistent_fn kFlavours[kNumFlavours] = {
     trim_persistent_kernel_m1,  trim_persistent_kernel_m2,  trim_persistent_kernel_m4,
     trim_persistent_kernel_m15, trim_persistent_kernel_m9,  trim_persistent_kernel_m10,
-    trim_persistent_kernel_m12, trim_persistent_kernel_m17};
+    trim_persistent_kernel_m12, trim_persistent_kernel_m17, trim_persistent_kernel_m34,
+    trim_persistent_kernel_m36};
 
 // launch shapes are a property of the device and the block size: computed once
 // per (device, block_threads, ctas_per_sm) for the whole process
@@ -533,6 +537,69 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
   return TRIM_OK;
 }
 
+// A context over an implicit graph: O(n) state only; m is the degree sum,
+// computed on the device.
+trim_err_t create_implicit_impl(const trim_implicit_graph_t* g, void* stream, uint32_t flags,
+                                trim_ctx* c) {
+  const uint64_t n64 = (uint64_t)g->nC + g->nR + g->nT;
+  if (n64 > (1u << 31)) return fail(c, TRIM_ERR_TOO_LARGE, "n must be <= 2^31");
+  if (g->nR && !g->nC) return fail(c, TRIM_ERR_INVALID_ARG, "a reaching set needs a core");
+  if (g->c_kmin > g->c_kmax || g->r_kmin > g->r_kmax || g->t_kmin > g->t_kmax)
+    return fail(c, TRIM_ERR_INVALID_ARG, "degree bounds: kmin > kmax");
+  if ((g->nC && g->c_kmax > (1u << 20)) || (g->nR && g->r_kmax > (1u << 20)) ||
+      g->t_kmax > (1u << 20))
+    return fail(c, TRIM_ERR_TOO_LARGE, "degrees above 2^20");
+  TRY(check_device(c, &c->device, &c->sm_count));
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->flags = flags;
+  c->n = (uint32_t)n64;
+  c->implicit = true;
+  c->ig = *g;
+  default_params(&c->params);
+  CK(cudaEventCreate(&c->ev0));
+  CK(cudaEventCreate(&c->ev1));
+  const size_t n = c->n;
+  if (flags & TRIM_FLAG_ROUND_LOG) c->rlog_cap = (uint32_t)std::min<uint64_t>(n + 1, 1u << 20);
+  ArenaPlan A;
+  const size_t a_level = A.add<uint32_t>(n), a_supp = A.add<uint32_t>(n);
+  const size_t a_shead = A.add<uint32_t>(n), a_snext = A.add<uint32_t>(n);
+  const size_t a_scnt = A.add<uint32_t>(n), a_soff = A.add<uint32_t>(n + 1);
+  const size_t a_slist = A.add<uint32_t>(n), a_log = A.add<uint32_t>(n);
+  const size_t a_roff = A.add<uint32_t>(n + 2), a_live0 = A.add<uint32_t>(n);
+  const size_t a_live1 = A.add<uint32_t>(n), a_bsum = A.add<uint32_t>(8192);
+  const size_t a_ctrl = A.add<Ctrl>(1), a_m = A.add<unsigned long long>(1);
+  const size_t a_rlog = c->rlog_cap ? A.add<trim_round_rec_t>(c->rlog_cap) : 0;
+  char* base = nullptr;
+  TRY(dalloc(c, &base, A.bytes));
+  auto at = [&](size_t o) { return reinterpret_cast<uint32_t*>(base + o); };
+  c->level = at(a_level); c->supp = at(a_supp); c->cnt = nullptr;
+  c->s_head = at(a_shead); c->s_next = at(a_snext); c->s_cnt = at(a_scnt);
+  c->s_off = at(a_soff); c->s_list = at(a_slist); c->log = at(a_log); c->roff = at(a_roff);
+  c->live0 = at(a_live0); c->live1 = at(a_live1); c->bsum = at(a_bsum);
+  c->ctrl = reinterpret_cast<Ctrl*>(base + a_ctrl);
+  if (c->rlog_cap) c->rlog = reinterpret_cast<trim_round_rec_t*>(base + a_rlog);
+  CK(cudaMemsetAsync(c->s_cnt, 0, n * 4, c->stream));
+  // m = the sum of the degrees
+  unsigned long long* dm = reinterpret_cast<unsigned long long*>(base + a_m);
+  CK(cudaMemsetAsync(dm, 0, 8, c->stream));
+  Dev D{};
+  D.n = c->n;
+  D.ig = c->ig;
+  trim_implicit_degree_sum_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(D, dm);
+  CK(cudaGetLastError());
+  unsigned long long hm = 0;
+  CK(cudaMemcpyAsync(&hm, dm, 8, cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync_check(c));
+  if (hm > (1ull << 32) - 64) return fail(c, TRIM_ERR_TOO_LARGE, "m must be <= 2^32 - 64");
+  c->m = hm;
+  c->h_ctrl = take_ctrl_slot();
+  c->h_ctrl_pinned = c->h_ctrl != nullptr;
+  if (!c->h_ctrl) c->h_ctrl = new (std::nothrow) Ctrl();
+  if (!c->h_ctrl) return fail(c, TRIM_ERR_OOM, "host allocation failed");
+  TRY(compute_grid(c));
+  return TRIM_OK;
+}
+
 // AC-4 work list (one entry per removed vertex with in-edges) and the owner
 // index of every 32-edge chunk of its in-edge prefix; allocated on first use.
 trim_err_t ensure_work_list(trim_ctx* c) {
@@ -564,6 +631,12 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
                        uint32_t commit_after = 0, bool inout = false) {
   if ((int)variant < 0 || variant > TRIM_SCHED_SCRIPTED)
     return fail(c, TRIM_ERR_INVALID_ARG, "unknown variant");
+  if (c->implicit) {
+    if ((variant != TRIM_AC6_SUPPORT && variant != TRIM_AC3_PULL) || inout || seg_flavour >= 0)
+      return fail(c, TRIM_ERR_INVALID_ARG,
+                  "an implicit graph runs TRIM_AC6_SUPPORT or TRIM_AC3_PULL only");
+    if (c->has_mask) return fail(c, TRIM_ERR_INVALID_ARG, "an implicit graph takes no dead mask");
+  }
   if (inout) {
     if (c->has_mask) return fail(c, TRIM_ERR_INVALID_ARG, "trim_run_inout does not take a dead mask");
     if (c->ioff == nullptr) TRY(build_transpose(c));
@@ -621,6 +694,7 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   D.chunk_first = c->chunk_first; D.bsum = c->bsum; D.C = c->ctrl;
   D.cnt_in = c->cnt_in; D.w4_orow = c->w4_orow; D.w4_din = c->w4_din;
   D.mask = c->has_mask ? c->mask : nullptr;
+  D.ig = c->ig;
   if (inout) D.chunk_first = c->chunk_io;
   D.sbuf_cap = kSbufCap;
   D.rlog = c->rlog; D.rlog_cap = c->rlog_cap;
@@ -637,7 +711,8 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   if (variant >= TRIM_SCHED_HEURISTIC && seg_flavour >= 0) D.flags |= trimk::F_LIVE_EDGES;
   // a fixed variant runs on its lean single-variant flavour
   int flavour = kFlavourAll;
-  if (inout) flavour = kFlavourInout;
+  if (c->implicit) flavour = variant == TRIM_AC6_SUPPORT ? kFlavourImplicitAC6 : kFlavourImplicitAC3;
+  else if (inout) flavour = kFlavourInout;
   else if (variant <= TRIM_AC3_PULL) flavour = (int)variant;
   else if (seg_flavour >= 0) flavour = seg_flavour;
   c->last_dev = D;
@@ -877,9 +952,29 @@ trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void
   return TRIM_OK;
 }
 
+trim_err_t trim_create_implicit(const trim_implicit_graph_t* g, void* cuda_stream, uint32_t flags,
+                                trim_ctx** out) {
+  if (!g || !out) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null graph or out");
+  if (flags & ~(TRIM_FLAG_STATS | TRIM_FLAG_ROUND_LOG))
+    return fail(nullptr, TRIM_ERR_INVALID_ARG, "flags: TRIM_FLAG_STATS, TRIM_FLAG_ROUND_LOG only");
+  trim_ctx* c = new (std::nothrow) trim_ctx();
+  if (!c) return fail(nullptr, TRIM_ERR_OOM, "host allocation failed");
+  trim_err_t e = create_implicit_impl(g, cuda_stream, flags, c);
+  if (e != TRIM_OK) {
+    g_create_error = c->err;
+    release(c);
+    delete c;
+    return e;
+  }
+  *out = c;
+  return TRIM_OK;
+}
+
 trim_err_t trim_run(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats) {
   if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
   c->last_segments = 1;
+  if (c->implicit && variant != TRIM_AC6_SUPPORT && variant != TRIM_AC3_PULL)
+    return fail(c, TRIM_ERR_INVALID_ARG, "an implicit graph runs TRIM_AC6_SUPPORT or TRIM_AC3_PULL only");
   if (variant >= TRIM_SCHED_HEURISTIC && variant <= TRIM_SCHED_SCRIPTED)
     return run_segmented(c, variant, stats);
   TRY(enqueue_run(c, variant));
@@ -907,6 +1002,7 @@ trim_err_t trim_sync(trim_ctx* c, trim_run_stats_t* stats) {
 trim_err_t trim_batch_run(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
                           trim_variant_t variant, trim_run_stats_t* stats) {
   if (!c || !graph_off || G == 0) return fail(c, TRIM_ERR_INVALID_ARG, "null argument or G = 0");
+  if (c->implicit) return fail(c, TRIM_ERR_INVALID_ARG, "batched runs need a CSR");
   if (graph_off[0] != 0 || graph_off[G] != c->n)
     return fail(c, TRIM_ERR_INVALID_ARG, "graph_off must start at 0 and end at n");
   for (uint32_t g = 0; g < G; ++g)

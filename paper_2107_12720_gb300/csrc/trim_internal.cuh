@@ -139,6 +139,9 @@ struct Dev {
   // vertex sampling (trim_set_dead_mask): mask[v] != 0 marks a vertex that is
   // DEAD from the start; nullable
   const uint8_t* __restrict__ mask;
+  // implicit graph (trim_create_implicit): successors computed on the fly by
+  // the implicit flavours; off/tgt are null then
+  trim_implicit_graph_t ig;
   uint32_t* bsum;     // per-CTA scratch of the grid-wide scan
   uint32_t sbuf_cap;  // entries of each CTA append buffer (dynamic shared memory)
   uint32_t resume;    // 1: continue the run from Ctrl::saved instead of starting it
@@ -230,6 +233,9 @@ __global__ void trim_persistent_kernel_m10(trimk::Dev D);  // AC-6 + schedulers 
 __global__ void trim_persistent_kernel_m12(trimk::Dev D);  // AC-3 + schedulers (segments)
 __global__ void trim_persistent_kernel_m15(trimk::Dev D);  // all variants + schedulers
 __global__ void trim_persistent_kernel_m17(trimk::Dev D);  // in+out trimming (AC-4 pushes on G and G^T)
+__global__ void trim_persistent_kernel_m34(trimk::Dev D);  // AC-6 on an implicit graph
+__global__ void trim_persistent_kernel_m36(trimk::Dev D);  // AC-3 on an implicit graph
+__global__ void trim_implicit_degree_sum_kernel(trimk::Dev D, unsigned long long* m);
 __global__ void trim_reset_ctrl_kernel(trimk::Ctrl* C);
 __global__ void trim_status_kernel(const uint32_t* level, uint32_t n, uint8_t* status);
 __global__ void trim_mask_levels_kernel(uint32_t* level, const uint8_t* mask, uint32_t n);

@@ -68,6 +68,9 @@ constexpr int M_AC4 = 1, M_AC6 = 2, M_AC3 = 4, M_SCHED = 8;
 // in+out trimming: AC-4 pushes on both G^T (out-degree counters) and G
 // (in-degree counters); its own flavour, with no other variant
 constexpr int M_INOUT = 16;
+// implicit graph (Section 2.1, on-the-fly): successors computed, no CSR; with
+// AC-6 (34) or AC-3 (36) only
+constexpr int M_IMPLICIT = 32;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int MAX_WARPS = 16;   // blockDim.x <= 512
 constexpr int WBUF = 64;        // per-warp staging of supporting-set members
@@ -168,6 +171,75 @@ __device__ __forceinline__ unsigned owner_of(unsigned excl, unsigned k) {
     if (cand < 32u && ex <= k) lo = cand;
   }
   return lo;
+}
+
+// ------------------------------------------------------------------ rows
+
+#if TRIM_MODES & 32
+// The implicit planted graph of trim_create_implicit (include/trim.h gives the
+// definition): SplitMix64 (Steele, Lea & Flood) as a counter-based generator,
+// key(v) = mix(seed ^ mix(salt + v + GAMMA)), word(v, i) = mix(key + (i+1) GAMMA),
+// and Lemire's multiply-shift for a uniform integer below k.
+constexpr uint64_t IG_GAMMA = 0x9E3779B97F4A7C15ull;
+__device__ __forceinline__ uint64_t ig_mix(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t ig_word(const Dev& D, uint32_t v, uint64_t i) {
+  const uint64_t key = ig_mix(D.ig.seed ^ ig_mix(D.ig.salt + v + IG_GAMMA));
+  return ig_mix(key + (i + 1ull) * IG_GAMMA);
+}
+__device__ __forceinline__ uint32_t ig_below(uint64_t w, uint64_t k) {
+  return (uint32_t)__umul64hi(w, k);
+}
+// number of successors of v
+__device__ uint32_t ig_degree(const Dev& D, uint32_t v) {
+  const trim_implicit_graph_t& g = D.ig;
+  const uint64_t w0 = ig_word(D, v, 0);
+  const uint32_t nCR = g.nC + g.nR;
+  if (v < g.nC) return g.c_kmin + ig_below(w0, (uint64_t)g.c_kmax - g.c_kmin + 1u);
+  if (v < nCR) return g.r_kmin + ig_below(w0, (uint64_t)g.r_kmax - g.r_kmin + 1u);
+  const uint32_t rank = v - nCR;
+  const uint32_t k = g.t_kmin + ig_below(w0, (uint64_t)g.t_kmax - g.t_kmin + 1u);
+  if (g.n_chains == 0u) return rank < g.t_sinks ? 0u : k;
+  return rank < g.n_chains ? 0u : 1u + k;
+}
+// successor j of v (j below its degree)
+__device__ uint32_t ig_successor(const Dev& D, uint32_t v, uint32_t j) {
+  const trim_implicit_graph_t& g = D.ig;
+  const uint64_t w = ig_word(D, v, 1ull + j);
+  const uint32_t nCR = g.nC + g.nR;
+  if (v < g.nC) return ig_below(w, g.nC);
+  if (v < nCR) return ig_below(w, j == 0u ? g.nC : nCR);
+  const uint32_t rank = v - nCR;
+  if (g.n_chains == 0u) return nCR + ig_below(w, rank);
+  if (j == 0u) return v - g.n_chains;
+  return nCR + ig_below(w, (uint64_t)(rank / g.n_chains) * g.n_chains);
+}
+#endif
+
+// Row access of the scans: out-CSR loads, or computed successors on an
+// implicit graph (where s is unused).
+__device__ __forceinline__ void row_bounds(const Dev& D, uint32_t v, uint32_t& s, uint32_t& d) {
+#if TRIM_MODES & 32
+  s = 0u;
+  d = ig_degree(D, v);
+#else
+  s = __ldg(&D.off[v]);
+  d = __ldg(&D.off[v + 1]) - s;
+#endif
+}
+__device__ __forceinline__ uint32_t row_target(const Dev& D, uint32_t v, uint32_t s, uint32_t j) {
+#if TRIM_MODES & 32
+  (void)s;
+  return ig_successor(D, v, j);
+#else
+  (void)v;
+  return __ldg(&D.tgt[s + j]);
+#endif
 }
 
 // ------------------------------------------------------------------ appends
@@ -637,15 +709,15 @@ __device__ __forceinline__ void stats_publish(const Dev& D, Cta& B) {
 // Thread-level forward scan of v's successors from position i (row start s,
 // length d): returns the first position whose target is not removed before
 // round r, or d. At most `batches` x 4 edges; *resolved tells whether it ended.
-__device__ __forceinline__ uint32_t scan_thread(const Dev& D, uint32_t s, uint32_t d, uint32_t i,
-                                                uint32_t r, int batches, bool& resolved,
-                                                Counters& K) {
+__device__ __forceinline__ uint32_t scan_thread(const Dev& D, uint32_t v, uint32_t s, uint32_t d,
+                                                uint32_t i, uint32_t r, int batches,
+                                                bool& resolved, Counters& K) {
   for (int b = 0; b < batches; ++b) {
     if (i >= d) { resolved = true; return d; }
     const uint32_t nb = min(4u, d - i);
     uint32_t t[4], lv[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) t[q] = (q < (int)nb) ? __ldg(&D.tgt[s + i + q]) : 0u;
+    for (int q = 0; q < 4; ++q) t[q] = (q < (int)nb) ? row_target(D, v, s, i + q) : 0u;
 #pragma unroll
     for (int q = 0; q < 4; ++q) lv[q] = (q < (int)nb) ? ldcg(&D.level[t[q]]) : 0u;
     K.edges += nb;
@@ -660,8 +732,8 @@ __device__ __forceinline__ uint32_t scan_thread(const Dev& D, uint32_t s, uint32
 
 // Warp-collective: finishes the scans of lanes with !resolved, one lane at a
 // time, 32 successors per step (ballot picks the first live one).
-__device__ __forceinline__ void scan_warp_finish(const Dev& D, bool& resolved, uint32_t s,
-                                                 uint32_t d, uint32_t& i, uint32_t r,
+__device__ __forceinline__ void scan_warp_finish(const Dev& D, bool& resolved, uint32_t v,
+                                                 uint32_t s, uint32_t d, uint32_t& i, uint32_t r,
                                                  Counters& K) {
   const unsigned lane = lane_id();
   unsigned pend = __ballot_sync(FULL, !resolved);
@@ -669,12 +741,13 @@ __device__ __forceinline__ void scan_warp_finish(const Dev& D, bool& resolved, u
     const int src = __ffs(pend) - 1;
     pend &= pend - 1;
     const uint32_t ss = __shfl_sync(FULL, s, src), dd = __shfl_sync(FULL, d, src);
+    const uint32_t vv = __shfl_sync(FULL, v, src);
     uint32_t ii = __shfl_sync(FULL, i, src);
     uint32_t found = dd;
     while (ii < dd) {
       const uint32_t k = ii + lane;
       bool live = false;
-      if (k < dd) live = ldcg(&D.level[__ldg(&D.tgt[ss + k])]) >= r;
+      if (k < dd) live = ldcg(&D.level[row_target(D, vv, ss, k)]) >= r;
       const unsigned b = __ballot_sync(FULL, live);
       if (lane == 0) K.edges += min(32u, dd - ii);
       if (b) { found = ii + __ffs(b) - 1; break; }
@@ -1305,12 +1378,11 @@ __device__ ROUND_FN void ac3_round(const Dev& D, Cta& B, const Sched& S, uint32_
     uint32_t s = 0, d = 0, i0 = 0, i = 0;
     bool resolved = true;
     if (alive) {
-      s = __ldg(&D.off[v]);
-      d = __ldg(&D.off[v + 1]) - s;
+      row_bounds(D, v, s, d);
       i0 = ldcg(&D.supp[v]);
-      i = scan_thread(D, s, d, i0, r, 2, resolved, K);
+      i = scan_thread(D, v, s, d, i0, r, 2, resolved, K);
     }
-    scan_warp_finish(D, resolved, s, d, i, r, K);
+    scan_warp_finish(D, resolved, v, s, d, i, r, K);
     const bool dies = alive && i >= d;
     const bool stays = alive && !dies;
     if (stays && i != i0) D.supp[v] = i;
@@ -1332,15 +1404,14 @@ __device__ __forceinline__ void ac6_rescan(const Dev& D, Cta& B, bool valid, uin
   uint32_t s = 0, d = 0, i = 0;
   bool resolved = true;
   if (alive) {
-    s = __ldg(&D.off[v]);
-    d = __ldg(&D.off[v + 1]) - s;
-    i = scan_thread(D, s, d, ldcg(&D.supp[v]) + 1u, r, 2, resolved, K);
+    row_bounds(D, v, s, d);
+    i = scan_thread(D, v, s, d, ldcg(&D.supp[v]) + 1u, r, 2, resolved, K);
   }
-  scan_warp_finish(D, resolved, s, d, i, r, K);
+  scan_warp_finish(D, resolved, v, s, d, i, r, K);
   const bool dies = alive && i >= d;
   if (alive && !dies) {
     D.supp[v] = i;
-    const uint32_t t = __ldg(&D.tgt[s + i]);
+    const uint32_t t = row_target(D, v, s, i);
     D.s_next[v] = atomicExch(&D.s_head[t], v);
   }
   K.cand += valid ? 1 : 0;
@@ -1402,16 +1473,15 @@ __device__ ROUND_FN bool ac6_entry(const Dev& D, Cta& B, const Sched& S, uint32_
     uint32_t s = 0, d = 0, i0 = 0, i = 0;
     bool resolved = true;
     if (alive) {
-      s = __ldg(&D.off[v]);
-      d = __ldg(&D.off[v + 1]) - s;
+      row_bounds(D, v, s, d);
       i0 = ldcg(&D.supp[v]);
-      i = scan_thread(D, s, d, i0, r, 2, resolved, K);
+      i = scan_thread(D, v, s, d, i0, r, 2, resolved, K);
     }
-    scan_warp_finish(D, resolved, s, d, i, r, K);
+    scan_warp_finish(D, resolved, v, s, d, i, r, K);
     const bool dies = alive && i >= d;
     if (alive && !dies) {
       if (i != i0) D.supp[v] = i;
-      const uint32_t t = __ldg(&D.tgt[s + i]);
+      const uint32_t t = row_target(D, v, s, i);
       D.s_next[v] = t;  // parked here until the scatter below
       atomicAdd(&D.s_cnt[t], 1u);
     }
@@ -1549,8 +1619,13 @@ __device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32
     for (int q = 0; q < U; ++q) {
       const uint32_t v = base + q * 32u + lane;
       const bool has = v < n;
+#if TRIM_MODES & 32
+      o0[q] = 0u;
+      o1[q] = has ? ig_degree(D, v) : 0u;
+#else
       o0[q] = has ? __ldg(&D.off[v]) : 0u;
       o1[q] = has ? __ldg(&D.off[v + 1]) : 0u;
+#endif
       i0[q] = (has && rows) ? __ldg(&D.ioff[v]) : 0u;
       i1[q] = (has && rows) ? __ldg(&D.ioff[v + 1]) : 0u;
     }
@@ -1580,7 +1655,7 @@ __device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32
   }
 }
 
-#if !(TRIM_MODES & 16)
+#if !(TRIM_MODES & 48)
 // Initial pass with a dead mask (vertex sampling, Section 9): a masked vertex
 // is DEAD from the start: level 0 (removed before round 1 for every variant),
 // counter 0 (a decrement can never return 1), never on the work list, not
@@ -1704,7 +1779,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     start_round(D, 0);
     if (threadIdx.x == 0) B.w4_wide = (MODES & M_INOUT) ? 0u : 1u;
     __syncthreads();
-#if !(TRIM_MODES & 16)
+#if !(TRIM_MODES & 48)
     if (D.mask != nullptr) init_round_masked(D, B, gwarp, nwarps);
     else
 #endif
@@ -1777,3 +1852,14 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
 
 // ---------------------------------------------------------------- helpers
 
+
+#if TRIM_MODES == 34
+// Edge count of an implicit graph: the sum of its degrees (one pass, n draws).
+__global__ void trim_implicit_degree_sum_kernel(Dev D, unsigned long long* m) {
+  unsigned long long acc = 0;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < D.n; v += gridDim.x * blockDim.x)
+    acc += ig_degree(D, v);
+  acc = warp_sum(acc);
+  if (lane_id() == 0 && acc) atomicAdd(m, acc);
+}
+#endif
