@@ -58,6 +58,8 @@ def _L():
             lib.or_certificate.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u8p]
             lib.or_peel_masked.restype = ctypes.c_uint32
             lib.or_peel_masked.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u8p, u32p, u8p]
+            lib.or_scc.restype = ctypes.c_uint32
+            lib.or_scc.argtypes = [ctypes.c_uint32, u32p, u32p, u32p]
             lib.or_peel_inout.restype = ctypes.c_uint32
             lib.or_peel_inout.argtypes = [ctypes.c_uint32, u32p, u32p, u32p, u32p, u32p, u8p]
             lib.or_certificate_inout.restype = ctypes.c_int64
@@ -174,3 +176,15 @@ def peel_masked(off, tgt, mask, csr_in=None):
     status = np.empty(max(n, 1), np.uint8)
     alpha = _L().or_peel_masked(n, off, off_in, tgt_in, mask, level, status)
     return level[:n], status[:n], int(alpha)
+
+
+def scc(off, tgt):
+    """Strongly connected components (Tarjan). Returns (comp, count) with
+    comp[v] = the smallest vertex id of v's component."""
+    off, tgt = _csr(off, tgt)
+    n = off.shape[0] - 1
+    comp = np.empty(max(n, 1), np.uint32)
+    k = _L().or_scc(n, off, tgt, comp)
+    if k == 0xFFFFFFFF:
+        raise MemoryError("or_scc: allocation failed")
+    return comp[:n], int(k)

@@ -30,6 +30,8 @@
  *   or_certificate_inout  its local conditions (exactly one assignment)
  *   or_peel_masked vertex-sampled inputs (Section 9, scalability experiment):
  *                  unsampled vertices are DEAD from the start
+ *   or_scc         strongly connected components (Section 1: the decomposition
+ *                  trimming feeds), Tarjan's algorithm, labelled canonically
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -353,4 +355,61 @@ uint32_t or_peel_masked(uint32_t n, const uint32_t* off, const uint32_t* off_in,
   for (uint32_t v = 0; v < n; ++v) status[v] = (level[v] == LIVE);
   free(cnt); free(cur); free(nxt);
   return alpha;
+}
+
+/* Strongly connected components (Section 1: FW-BW with trimming computes this
+ * decomposition; size-1 SCCs are the trimmable vertices). Tarjan's algorithm
+ * (one depth-first search; a vertex whose lowlink equals its own index roots a
+ * component made of the vertices above it on the component stack), written
+ * with an explicit call stack. comp[v] receives the smallest vertex id of v's
+ * component, which labels every decomposition the same way. Returns the number
+ * of components, or UINT32_MAX without memory. */
+uint32_t or_scc(uint32_t n, const uint32_t* off, const uint32_t* tgt, uint32_t* comp) {
+  const uint32_t NONE = 0xFFFFFFFFu;
+  uint32_t* index = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4);
+  uint32_t* low = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4);
+  uint8_t* on_stack = (uint8_t*)calloc((size_t)n + 1, 1);
+  uint32_t* cstack = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4); /* component stack */
+  uint32_t* call_v = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4); /* DFS call stack */
+  uint32_t* call_e = (uint32_t*)malloc((size_t)n * sizeof(uint32_t) + 4); /* next edge */
+  if (!index || !low || !on_stack || !cstack || !call_v || !call_e) {
+    free(index); free(low); free(on_stack); free(cstack); free(call_v); free(call_e);
+    return 0xFFFFFFFFu;
+  }
+  for (uint32_t v = 0; v < n; ++v) index[v] = NONE;
+  uint32_t next_index = 0, csp = 0, ncomp = 0;
+  for (uint32_t root = 0; root < n; ++root) {
+    if (index[root] != NONE) continue;
+    uint32_t depth = 0;
+    call_v[0] = root; call_e[0] = off[root];
+    index[root] = low[root] = next_index++;
+    cstack[csp++] = root; on_stack[root] = 1;
+    while (1) {
+      uint32_t v = call_v[depth];
+      if (call_e[depth] < off[v + 1]) {          /* visit the next successor */
+        uint32_t w = tgt[call_e[depth]++];
+        if (index[w] == NONE) {
+          index[w] = low[w] = next_index++;
+          cstack[csp++] = w; on_stack[w] = 1;
+          ++depth; call_v[depth] = w; call_e[depth] = off[w];
+        } else if (on_stack[w] && index[w] < low[v]) {
+          low[v] = index[w];
+        }
+        continue;
+      }
+      if (low[v] == index[v]) {                   /* v roots a component */
+        uint32_t start = csp, lo = v;
+        do { start--; if (cstack[start] < lo) lo = cstack[start]; } while (cstack[start] != v);
+        for (uint32_t i = start; i < csp; ++i) { comp[cstack[i]] = lo; on_stack[cstack[i]] = 0; }
+        csp = start;
+        ncomp++;
+      }
+      if (depth == 0) break;                      /* return to the caller */
+      --depth;
+      uint32_t u = call_v[depth];
+      if (low[v] < low[u]) low[u] = low[v];
+    }
+  }
+  free(index); free(low); free(on_stack); free(cstack); free(call_v); free(call_e);
+  return ncomp;
 }
