@@ -523,6 +523,18 @@ def split_by_size(P, g, args, flush, stream, max_n=4096, max_m=65536, steps=20):
     return out
 
 
+def scc_timing(t, g, steps=3):
+    """SCC decomposition of the graph (trim_run_scc: in+out trimming, size-2
+    trimming, forward-backward steps), elapsed time on the stream."""
+    t.run_scc(device=True)
+    runs = [t.run_scc(device=True)[1] for _ in range(steps)]
+    last = runs[-1]
+    out = dict(last, ms=statistics.mean(r["ms"] for r in runs))
+    print(f"# scc: {out['ms']:.3f} ms, {last['components']} components, steps {last['fwbw_steps']}",
+          file=sys.stderr, flush=True)
+    return out
+
+
 def vertex_sampling(P, t, g, flush, ratios=(0.1, 0.3, 0.5, 0.7, 0.9, 1.0), steps=10):
     """Section 9's scalability experiment on this graph: a share `ratio` of
     the vertices is sampled (a fixed uniform draw per vertex), the others are
@@ -601,10 +613,12 @@ def extra_workload(P, idx, args, flush, stream, model):
                                label=f"[{idx}] ")
         if idx == 1:
             sampling = vertex_sampling(P, t, g, flush)
+        scc = scc_timing(t, g)
     out = {"workload": wname, "n": g.n, "m": g.m, "variants": sweep,
            "schedules": schedules_summary(sweep)}
     if sampling:
         out["vertex_sampling"] = sampling
+    out["scc"] = scc
     if batched:
         out["graphs"] = int(len(g.graph_off) - 1)
         out["timing"] = ("CUDA events around trim_batch_run: one replayed CUDA graph "

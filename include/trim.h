@@ -229,6 +229,42 @@ typedef struct {
 trim_err_t trim_create_implicit(const trim_implicit_graph_t* g, void* cuda_stream, uint32_t flags,
                                 trim_ctx** out);
 
+/* ---- SCC decomposition (Section 1: the use trimming is made for) ----
+ * trim_run_scc labels every vertex with its strongly connected component:
+ * comp[v] = the smallest vertex id of v's component (the same labels whatever
+ * the order of the work). Steps, all on the device, driven from the host:
+ *  1. in+out trimming (trim_run_inout): every removed vertex is a size-1
+ *     component (it has no in-edge or no out-edge among the others);
+ *  2. size-2 trimming: two open vertices that are each other's only open
+ *     successor (or each other's only open predecessor) form a component;
+ *  3. forward-backward steps (Section 1's FW-BW, from every vertex at once):
+ *     forward, every open vertex learns the smallest open vertex that reaches
+ *     it (label propagation along G); a vertex r that keeps its own label is
+ *     reached by no smaller vertex, and the backward search from r through
+ *     G^T among the vertices labelled r collects exactly r's component, whose
+ *     smallest member r is. Every step closes at least the component of the
+ *     smallest open vertex; independent parts of the graph (the graphs of a
+ *     batch) advance together. Before every step, trimming passes remove the
+ *     open vertices without an open successor or predecessor (size-1
+ *     components that became trimmable, as Figure 1's v6 and v7 do once the
+ *     large components are gone).
+ * comp: n uint32, on the device if out_on_device else on the host. Needs G^T
+ * (csr_in, or built on the device). Overwrites the context's level array (with
+ * the in+out trimming of step 1). stats may be NULL. Device memory ~ 24 n
+ * bytes is allocated on first use. Not for implicit graphs or with a dead mask
+ * (TRIM_ERR_INVALID_ARG). */
+typedef struct {
+  uint32_t components;       /* number of strongly connected components              */
+  uint32_t trimmed_size1;    /* size-1 components removed by step 1                  */
+  uint32_t trimmed_size2;    /* size-2 components found by step 2                     */
+  uint32_t trimmed_in_steps; /* size-1 components removed by the passes of step 3     */
+  uint32_t fwbw_steps;       /* forward-backward steps of step 3                       */
+  uint32_t search_levels;    /* frontier levels of the label propagations and backward
+                                searches, all steps                                     */
+  float ms;                  /* elapsed time on the stream, steps 1-3                 */
+} trim_scc_stats_t;
+trim_err_t trim_run_scc(trim_ctx* ctx, uint32_t* comp, int out_on_device, trim_scc_stats_t* stats);
+
 /* Vertex sampling (Section 9's scalability experiment samples vertices by setting
  * the unsampled ones DEAD before trimming). mask: n bytes, mask[v] != 0 makes v
  * DEAD from the start (status 0, level TRIM_MASKED); on the device if on_device

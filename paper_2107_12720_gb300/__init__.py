@@ -26,7 +26,7 @@ from .abi import (trim_batch_run, trim_create, trim_create_implicit, trim_defaul
                   trim_destroy,
                   trim_get_params, trim_get_round_log, trim_last_error, trim_level,
                   trim_level_device_ptr, trim_mlp_adam_step, trim_mlp_forward, trim_mlp_loss_grad,
-                  trim_mlp_scratch_bytes, trim_run, trim_run_async, trim_run_inout,
+                  trim_mlp_scratch_bytes, trim_run, trim_run_async, trim_run_inout, trim_run_scc,
                   trim_set_alloc_limit, trim_set_dead_mask,
                   trim_set_model, trim_set_params, trim_set_schedule, trim_status, trim_sync)
 
@@ -141,6 +141,18 @@ class Trimmer:
         if m.shape[0] != self.n:
             raise TrimError(1, "mask must have n entries")
         trim_set_dead_mask(self.ctx, m.ctypes.data, 0)
+
+    def run_scc(self, device: bool = False):
+        """SCC decomposition (trim_run_scc): returns (comp, stats) with comp[v]
+        the smallest vertex id of v's strongly connected component."""
+        import torch
+        if device:
+            comp = torch.empty(self.n, dtype=torch.int32, device="cuda")
+            s = trim_run_scc(self.ctx, comp.data_ptr(), 1)
+        else:
+            comp = np.empty(self.n, np.uint32)
+            s = trim_run_scc(self.ctx, comp.ctypes.data, 0)
+        return comp, {k: getattr(s, k) for k, _ in s._fields_}
 
     def run_inout(self) -> dict:
         """In+out trimming (no live successor or no live predecessor removes a

@@ -51,6 +51,12 @@ class TrimImplicitGraph(ctypes.Structure):
                                        "t_sinks", "t_kmin", "t_kmax", "n_chains")]
 
 
+class TrimSccStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint32) for k in ("components", "trimmed_size1", "trimmed_size2",
+                                               "trimmed_in_steps", "fwbw_steps",
+                                               "search_levels")] + [("ms", ctypes.c_float)]
+
+
 class TrimRunStats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint32), ("n_dead", ctypes.c_uint32),
                 ("device_ms", ctypes.c_float), ("edges_inspected", ctypes.c_uint64),
@@ -75,6 +81,7 @@ SIGNATURES = [
                          ctypes.POINTER(_P)]),
     ("trim_run", _I, [_P, _I, ctypes.POINTER(TrimRunStats)]),
     ("trim_run_inout", _I, [_P, ctypes.POINTER(TrimRunStats)]),
+    ("trim_run_scc", _I, [_P, _P, _I, ctypes.POINTER(TrimSccStats)]),
     ("trim_create_implicit", _I, [ctypes.POINTER(TrimImplicitGraph), _P, _U32,
                                   ctypes.POINTER(_P)]),
     ("trim_set_dead_mask", _I, [_P, _P, _I]),
@@ -155,6 +162,12 @@ def trim_create_implicit(graph: TrimImplicitGraph, stream, flags: int):
     ctx = ctypes.c_void_p()
     check(lib().trim_create_implicit(ctypes.byref(graph), stream, flags, ctypes.byref(ctx)), None)
     return ctx
+
+
+def trim_run_scc(ctx, comp, out_on_device: int) -> TrimSccStats:
+    s = TrimSccStats()
+    check(lib().trim_run_scc(ctx, _ptr(comp), out_on_device, ctypes.byref(s)), ctx)
+    return s
 
 
 def trim_run_inout(ctx) -> TrimRunStats:

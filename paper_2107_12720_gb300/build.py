@@ -29,6 +29,7 @@ UNITS = [("trim_kernels.cu", ["-DTRIM_MODES=1"], "trim_kernels_m1.o"),
          ("trim_kernels.cu", ["-DTRIM_MODES=34"], "trim_kernels_m34.o"),
          ("trim_kernels.cu", ["-DTRIM_MODES=36"], "trim_kernels_m36.o"),
          ("trim_aux.cu", [], "trim_aux.o"),
+         ("trim_scc.cu", [], "trim_scc.o"),
          ("trim_api.cu", [], "trim_api.o"),
          ("trim_noalloc.cu", [], "trim_noalloc.o"),
          ("mlp.cu", [], "mlp.o")]

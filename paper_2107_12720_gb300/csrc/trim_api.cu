@@ -48,6 +48,13 @@ struct trim_ctx {
   bool has_mask = false;
   bool implicit = false;      // trim_create_implicit: successors computed, no CSR
   trim_implicit_graph_t ig{};
+  // trim_run_scc: component labels, propagated labels, label-frontier stamps,
+  // backward-search marks, two frontiers, counters (allocated on first use)
+  uint32_t *scc_comp = nullptr, *scc_color = nullptr, *scc_fw = nullptr, *scc_bw = nullptr,
+           *scc_fa = nullptr, *scc_fb = nullptr;
+  unsigned long long* scc_cnt = nullptr;
+  uint32_t scc_stamp = 0;  // last search stamp: marks of earlier runs stay below it
+  cudaEvent_t scc_ev0 = nullptr, scc_ev1 = nullptr;
   Ctrl* ctrl = nullptr;
   Ctrl* h_ctrl = nullptr;  // host mirror of the control block for read-back
   bool h_ctrl_pinned = false;
@@ -209,6 +216,8 @@ void release(trim_ctx* c) {
   c->h_ctrl = nullptr;
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->scc_ev0) cudaEventDestroy(c->scc_ev0);
+  if (c->scc_ev1) cudaEventDestroy(c->scc_ev1);
 }
 
 trim_err_t check_device(trim_ctx* c, int* dev, int* sms) {
@@ -735,6 +744,178 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   return TRIM_OK;
 }
 
+trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read = false);
+
+// ---- SCC decomposition (trim_run_scc) ----
+
+trim_err_t ensure_scc(trim_ctx* c) {
+  if (c->scc_comp) return TRIM_OK;
+  const size_t n = c->n;
+  TRY(dalloc(c, &c->scc_comp, n));
+  TRY(dalloc(c, &c->scc_color, n));
+  TRY(dalloc(c, &c->scc_fw, n));
+  TRY(dalloc(c, &c->scc_bw, n));
+  TRY(dalloc(c, &c->scc_fa, n));
+  TRY(dalloc(c, &c->scc_fb, n));
+  TRY(dalloc(c, &c->scc_cnt, 4));
+  CK(cudaMemsetAsync(c->scc_fw, 0, n * 4, c->stream));  // marks hold search stamps (>= 1)
+  CK(cudaMemsetAsync(c->scc_bw, 0, n * 4, c->stream));
+  if (!c->scc_ev0) CK(cudaEventCreate(&c->scc_ev0));
+  if (!c->scc_ev1) CK(cudaEventCreate(&c->scc_ev1));
+  return TRIM_OK;
+}
+
+// reads counter i of the SCC counters (waits for the stream)
+trim_err_t scc_read(trim_ctx* c, int i, unsigned long long* v) {
+  CK(cudaMemcpyAsync(v, c->scc_cnt + i, 8, cudaMemcpyDeviceToHost, c->stream));
+  return sync_check(c);
+}
+
+// Runs frontier levels until the frontier is empty: the first frontier (k
+// vertices) is in c->scc_fa; `level` enqueues one level from fa (k vertices)
+// into fb, counting into the given device counter. Returns the levels run.
+template <class Level>
+trim_err_t scc_levels(trim_ctx* c, uint32_t k, Level level, uint32_t* levels) {
+  uint32_t* cnt32 = reinterpret_cast<uint32_t*>(c->scc_cnt + 3);
+  const int blocks = c->sm_count * 8;
+  uint32_t *fa = c->scc_fa, *fb = c->scc_fb;
+  while (k > 0) {
+    CK(cudaMemsetAsync(cnt32 + 1, 0, 4, c->stream));
+    const uint32_t warps_needed = std::min<uint32_t>(k, (uint32_t)blocks * 8u);
+    level(std::max<uint32_t>(1u, (warps_needed + 7u) / 8u), fa, k, fb, cnt32 + 1);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&k, cnt32 + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync_check(c));
+    std::swap(fa, fb);
+    ++*levels;
+  }
+  c->scc_fa = fa;  // the two frontier buffers may have traded places
+  c->scc_fb = fb;
+  return TRIM_OK;
+}
+
+// the next search stamp (marks of earlier searches stay below it; the mark
+// arrays are cleared before the counter could wrap)
+trim_err_t scc_next_stamp(trim_ctx* c, uint32_t* stamp) {
+  if (c->scc_stamp >= 0xFFFFFFF0u) {
+    CK(cudaMemsetAsync(c->scc_fw, 0, (size_t)c->n * 4, c->stream));
+    CK(cudaMemsetAsync(c->scc_bw, 0, (size_t)c->n * 4, c->stream));
+    c->scc_stamp = 0;
+  }
+  *stamp = ++c->scc_stamp;
+  return TRIM_OK;
+}
+
+trim_err_t run_scc(trim_ctx* c, uint32_t* out, int out_on_device, trim_scc_stats_t* stats) {
+  if (c->implicit) return fail(c, TRIM_ERR_INVALID_ARG, "SCC decomposition needs a CSR");
+  if (c->has_mask) return fail(c, TRIM_ERR_INVALID_ARG, "SCC decomposition takes no dead mask");
+  trim_scc_stats_t st{};
+  if (c->n == 0) {
+    if (stats) *stats = st;
+    return TRIM_OK;
+  }
+  TRY(ensure_scc(c));
+  CK(cudaEventRecord(c->scc_ev0, c->stream));
+  // 1. size-1 components: in+out trimming
+  TRY(enqueue_run(c, TRIM_AC4_PUSH, -1, 0, true));
+  TRY(finish_run(c, nullptr));
+  st.trimmed_size1 = c->last.n_dead;
+  const uint32_t n = c->n;
+  const int blocks = c->sm_count * 8;
+  scc_init_kernel<<<blocks, 256, 0, c->stream>>>(c->level, n, c->scc_comp, c->scc_color);
+  CK(cudaGetLastError());
+  // 2. size-2 components
+  CK(cudaMemsetAsync(c->scc_cnt, 0, 24, c->stream));
+  scc_trim2_single_kernel<<<blocks, 256, 0, c->stream>>>(c->off, c->tgt, c->ioff, c->itgt, n,
+                                                         c->scc_comp, c->scc_fa, c->scc_fb);
+  CK(cudaGetLastError());
+  scc_trim2_pair_kernel<<<blocks, 256, 0, c->stream>>>(n, c->scc_fa, c->scc_fb, c->scc_comp,
+                                                       c->scc_cnt);
+  CK(cudaGetLastError());
+  unsigned long long v = 0;
+  TRY(scc_read(c, 0, &v));
+  st.trimmed_size2 = (uint32_t)v;
+  // 3. steps: trimming passes, then label propagation along G (every open
+  // vertex learns the smallest open vertex that reaches it) and backward
+  // searches through G^T from the vertices that kept their own label
+  const uint32_t* off = c->off;
+  const uint32_t* tgt = c->tgt;
+  const uint32_t* ioff = c->ioff;
+  const uint32_t* itgt = c->itgt;
+  uint32_t* comp = c->scc_comp;
+  uint32_t* label = c->scc_color;
+  uint32_t* cnt32 = reinterpret_cast<uint32_t*>(c->scc_cnt + 3);
+  for (uint32_t step = 0; step <= n; ++step) {
+    for (int pass = 0; pass < 1024; ++pass) {  // trimming passes
+      CK(cudaMemsetAsync(c->scc_cnt + 1, 0, 8, c->stream));
+      scc_trim1_kernel<<<blocks, 256, 0, c->stream>>>(off, tgt, ioff, itgt, n, comp,
+                                                      c->scc_cnt + 1);
+      CK(cudaGetLastError());
+      TRY(scc_read(c, 1, &v));
+      st.trimmed_in_steps += (uint32_t)v;
+      if (v == 0) break;
+    }
+    // labels
+    CK(cudaMemsetAsync(c->scc_cnt + 2, 0, 16, c->stream));  // open count, two frontier counters
+    scc_label_start_kernel<<<blocks, 256, 0, c->stream>>>(n, comp, label, c->scc_fa, cnt32,
+                                                          c->scc_cnt + 2);
+    CK(cudaGetLastError());
+    TRY(scc_read(c, 2, &v));
+    if (v == 0) break;  // every vertex has its component
+    uint32_t k = 0;
+    CK(cudaMemcpyAsync(&k, cnt32, 4, cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync_check(c));
+    while (k > 0) {  // one stamp per level: a vertex joins a level's frontier once
+      uint32_t stamp = 0;
+      TRY(scc_next_stamp(c, &stamp));
+      uint32_t lv = 0;
+      uint32_t* fa = c->scc_fa;
+      uint32_t* fb = c->scc_fb;
+      CK(cudaMemsetAsync(cnt32 + 1, 0, 4, c->stream));
+      const uint32_t warps_needed = std::min<uint32_t>(k, (uint32_t)blocks * 8u);
+      scc_label_level_kernel<<<std::max<uint32_t>(1u, (warps_needed + 7u) / 8u), 256, 0,
+                               c->stream>>>(off, tgt, comp, label, c->scc_fw, stamp, fa, k, fb,
+                                            cnt32 + 1);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(&k, cnt32 + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+      TRY(sync_check(c));
+      std::swap(c->scc_fa, c->scc_fb);
+      (void)lv;
+      ++st.search_levels;
+    }
+    // backward searches from the roots
+    uint32_t stamp = 0;
+    TRY(scc_next_stamp(c, &stamp));
+    CK(cudaMemsetAsync(cnt32, 0, 4, c->stream));
+    scc_roots_start_kernel<<<blocks, 256, 0, c->stream>>>(n, comp, label, c->scc_bw, stamp,
+                                                          c->scc_fa, cnt32);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&k, cnt32, 4, cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync_check(c));
+    TRY(scc_levels(c, k,
+                   [&](uint32_t b, uint32_t* fa, uint32_t kk, uint32_t* fb, uint32_t* nc) {
+                     scc_search_level_kernel<<<b, 256, 0, c->stream>>>(
+                         ioff, itgt, comp, label, c->scc_bw, stamp, fa, kk, fb, nc);
+                   },
+                   &st.search_levels));
+    scc_close_kernel<<<blocks, 256, 0, c->stream>>>(n, comp, label, c->scc_bw, stamp, c->scc_cnt);
+    CK(cudaGetLastError());
+    ++st.fwbw_steps;
+  }
+  CK(cudaMemsetAsync(c->scc_cnt, 0, 8, c->stream));
+  scc_count_kernel<<<blocks, 256, 0, c->stream>>>(n, c->scc_comp, c->scc_cnt);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(c->scc_ev1, c->stream));
+  TRY(scc_read(c, 0, &v));
+  st.components = (uint32_t)v;
+  CK(cudaEventElapsedTime(&st.ms, c->scc_ev0, c->scc_ev1));
+  CK(cudaMemcpyAsync(out, c->scc_comp, (size_t)n * 4,
+                     out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  TRY(sync_check(c));
+  if (stats) *stats = st;
+  return TRIM_OK;
+}
+
 // Launches the next segment of a segmented run, resuming from the schedule
 // state the last segment saved: `flavour` runs with `mode` (the scheduled mode,
 // or a fixed variant for a committed stretch that hands back at stop_round).
@@ -754,7 +935,6 @@ trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base, uint32_t 
   return TRIM_OK;
 }
 
-trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read = false);
 
 // A scheduled run (heuristic, learned, scripted) on the lean kernels: each
 // segment is one cooperative launch. The scheduler runs on the flavour that
@@ -986,6 +1166,12 @@ trim_err_t trim_run_inout(trim_ctx* c, trim_run_stats_t* stats) {
   c->last_segments = 1;
   TRY(enqueue_run(c, TRIM_AC4_PUSH, -1, 0, true));
   return finish_run(c, stats);
+}
+
+trim_err_t trim_run_scc(trim_ctx* c, uint32_t* comp, int out_on_device, trim_scc_stats_t* stats) {
+  if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  if (!comp && c->n) return fail(c, TRIM_ERR_INVALID_ARG, "null comp");
+  return run_scc(c, comp, out_on_device, stats);
 }
 
 trim_err_t trim_run_async(trim_ctx* c, trim_variant_t variant) {

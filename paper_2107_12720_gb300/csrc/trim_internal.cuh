@@ -238,6 +238,34 @@ __global__ void trim_persistent_kernel_m36(trimk::Dev D);  // AC-3 on an implici
 __global__ void trim_implicit_degree_sum_kernel(trimk::Dev D, unsigned long long* m);
 __global__ void trim_reset_ctrl_kernel(trimk::Ctrl* C);
 __global__ void trim_status_kernel(const uint32_t* level, uint32_t n, uint8_t* status);
+// SCC decomposition (trim_scc.cu)
+__global__ void scc_init_kernel(const uint32_t* level, uint32_t n, uint32_t* comp, uint32_t* color);
+__global__ void scc_trim2_single_kernel(const uint32_t* off, const uint32_t* tgt,
+                                        const uint32_t* ioff, const uint32_t* itgt, uint32_t n,
+                                        const uint32_t* comp, uint32_t* out1, uint32_t* in1);
+__global__ void scc_trim2_pair_kernel(uint32_t n, const uint32_t* out1, const uint32_t* in1,
+                                      uint32_t* comp, unsigned long long* pairs);
+__global__ void scc_trim1_kernel(const uint32_t* off, const uint32_t* tgt, const uint32_t* ioff,
+                                 const uint32_t* itgt, uint32_t n, uint32_t* comp,
+                                 unsigned long long* removed);
+__global__ void scc_label_start_kernel(uint32_t n, const uint32_t* comp, uint32_t* label,
+                                       uint32_t* frontier, uint32_t* count,
+                                       unsigned long long* open);
+__global__ void scc_label_level_kernel(const uint32_t* off, const uint32_t* tgt,
+                                       const uint32_t* comp, uint32_t* label, uint32_t* inq,
+                                       uint32_t stamp, const uint32_t* frontier, uint32_t count,
+                                       uint32_t* next, uint32_t* next_count);
+__global__ void scc_roots_start_kernel(uint32_t n, const uint32_t* comp, const uint32_t* label,
+                                       uint32_t* mark, uint32_t stamp, uint32_t* frontier,
+                                       uint32_t* count);
+__global__ void scc_search_level_kernel(const uint32_t* rowoff, const uint32_t* rowtgt,
+                                        const uint32_t* comp, const uint32_t* color,
+                                        uint32_t* mark, uint32_t stamp, const uint32_t* frontier,
+                                        uint32_t count, uint32_t* next, uint32_t* next_count);
+__global__ void scc_close_kernel(uint32_t n, uint32_t* comp, const uint32_t* label,
+                                 const uint32_t* mark, uint32_t stamp,
+                                 unsigned long long* placed);
+__global__ void scc_count_kernel(uint32_t n, const uint32_t* comp, unsigned long long* count);
 __global__ void trim_mask_levels_kernel(uint32_t* level, const uint8_t* mask, uint32_t n);
 __global__ void trim_indeg_kernel(const uint32_t* tgt, uint64_t m, uint32_t n, uint32_t* cnt,
                                   uint32_t* bad);

@@ -44,10 +44,10 @@ def test_struct_layouts_match_header(lib, tmp_path):
     compiler makes of include/trim.h."""
     import subprocess
     from paper_2107_12720_gb300.abi import (TrimCsr, TrimImplicitGraph, TrimParams, TrimRoundRec,
-                                            TrimRunStats)
+                                            TrimRunStats, TrimSccStats)
     structs = {"trim_csr_t": TrimCsr, "trim_params_t": TrimParams,
                "trim_run_stats_t": TrimRunStats, "trim_round_rec_t": TrimRoundRec,
-               "trim_implicit_graph_t": TrimImplicitGraph}
+               "trim_implicit_graph_t": TrimImplicitGraph, "trim_scc_stats_t": TrimSccStats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "trim.h"', 'int main(void) {']
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
