@@ -68,6 +68,7 @@ struct Sched {
   // removals so far = log_len + skew and logged entry i of the count sits at
   // log position i - skew
   uint32_t skew;
+  uint32_t supp_valid;           // 1 once an AC-6 or AC-3 round set the support positions
   uint32_t lround;               // local rounds run so far (parity picks the barrier slot)
   unsigned long long lbase[2];   // value of each local-barrier slot after its last round
 };

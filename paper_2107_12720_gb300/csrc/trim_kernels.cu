@@ -716,8 +716,20 @@ __device__ __forceinline__ uint32_t scan_thread(const Dev& D, uint32_t v, uint32
     if (i >= d) { resolved = true; return d; }
     const uint32_t nb = min(4u, d - i);
     uint32_t t[4], lv[4];
+#if TRIM_MODES & 32
 #pragma unroll
     for (int q = 0; q < 4; ++q) t[q] = (q < (int)nb) ? row_target(D, v, s, i + q) : 0u;
+#else
+    // four targets on a 16-byte boundary (of the address: a caller's array may
+    // start anywhere) come with one load
+    if (nb == 4u && (reinterpret_cast<uintptr_t>(D.tgt + s + i) & 15u) == 0u) {
+      const uint4 x = __ldg(reinterpret_cast<const uint4*>(D.tgt + s + i));
+      t[0] = x.x; t[1] = x.y; t[2] = x.z; t[3] = x.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[q] = (q < (int)nb) ? __ldg(&D.tgt[s + i + q]) : 0u;
+    }
+#endif
 #pragma unroll
     for (int q = 0; q < 4; ++q) lv[q] = (q < (int)nb) ? ldcg(&D.level[t[q]]) : 0u;
     K.edges += nb;
@@ -898,6 +910,9 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
       L.ac3_list = L.live_out;
       L.live_in_len = live_count;
     }
+    // the first AC-6 or AC-3 round wrote the support position of every vertex
+    // still live (both sweep all live vertices when they first run)
+    if (L.variant == TRIM_AC6_SUPPORT || L.variant == TRIM_AC3_PULL) L.supp_valid = 1u;
   }
   L.bmax = max(L.bmax, max_din);  // the entries of F_r join the AC-4 backlog
   if (cta0) {
@@ -1379,13 +1394,13 @@ __device__ ROUND_FN void ac3_round(const Dev& D, Cta& B, const Sched& S, uint32_
     bool resolved = true;
     if (alive) {
       row_bounds(D, v, s, d);
-      i0 = ldcg(&D.supp[v]);
+      i0 = S.supp_valid ? ldcg(&D.supp[v]) : 0u;  // no support position yet: the row start
       i = scan_thread(D, v, s, d, i0, r, 2, resolved, K);
     }
     scan_warp_finish(D, resolved, v, s, d, i, r, K);
     const bool dies = alive && i >= d;
     const bool stays = alive && !dies;
-    if (stays && i != i0) D.supp[v] = i;
+    if (stays && (i != i0 || !S.supp_valid)) D.supp[v] = i;
     K.swept += has ? 1 : 0;
     append_dead(D, B, dies, v, r, Lout, false, false, 0, 0, d);
     append_live(D, B, stays, v, r, Lout);
@@ -1474,13 +1489,13 @@ __device__ ROUND_FN bool ac6_entry(const Dev& D, Cta& B, const Sched& S, uint32_
     bool resolved = true;
     if (alive) {
       row_bounds(D, v, s, d);
-      i0 = ldcg(&D.supp[v]);
+      i0 = S.supp_valid ? ldcg(&D.supp[v]) : 0u;  // no support position yet: the row start
       i = scan_thread(D, v, s, d, i0, r, 2, resolved, K);
     }
     scan_warp_finish(D, resolved, v, s, d, i, r, K);
     const bool dies = alive && i >= d;
     if (alive && !dies) {
-      if (i != i0) D.supp[v] = i;
+      if (i != i0 || !S.supp_valid) D.supp[v] = i;
       const uint32_t t = row_target(D, v, s, i);
       D.s_next[v] = t;  // parked here until the scatter below
       atomicAdd(&D.s_cnt[t], 1u);
@@ -1611,7 +1626,6 @@ __device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32
   const unsigned lane = lane_id();
   const uint32_t n = D.n;
   const bool w4 = (D.flags & F_AC4_POSSIBLE) != 0;
-  const bool w6 = (D.flags & (F_AC6_POSSIBLE | F_AC3_POSSIBLE)) != 0;
   const bool rows = D.ioff != nullptr;
   for (uint32_t base = gwarp * (32u * U); base < n; base += nwarps * (32u * U)) {
     uint32_t o0[U], o1[U], i0[U], i1[U];
@@ -1626,9 +1640,22 @@ __device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32
       o0[q] = has ? __ldg(&D.off[v]) : 0u;
       o1[q] = has ? __ldg(&D.off[v + 1]) : 0u;
 #endif
+#if TRIM_MODES & 16
+      // in+out needs every vertex's in-degree
       i0[q] = (has && rows) ? __ldg(&D.ioff[v]) : 0u;
       i1[q] = (has && rows) ? __ldg(&D.ioff[v + 1]) : 0u;
+#endif
     }
+#if !(TRIM_MODES & 16)
+    // one-sided: only the vertices removed here (no out-edge) need their G^T
+    // row, for their work-list entry; the loads of all four blocks go out together
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const bool sink = base + q * 32u + lane < n && o1[q] == o0[q];
+      i0[q] = (sink && rows) ? __ldg(&D.ioff[base + q * 32u + lane]) : 0u;
+      i1[q] = (sink && rows) ? __ldg(&D.ioff[base + q * 32u + lane + 1]) : 0u;
+    }
+#endif
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       const uint32_t v = base + q * 32u + lane;
@@ -1647,7 +1674,6 @@ __device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32
       if (has) {
         D.level[v] = d ? LIVE : 0u;
         if (w4) D.cnt[v] = d;
-        if (w6) D.supp[v] = 0u;
       }
       append_dead(D, B, has && d == 0u, v, 0u, D.live0, true, true, i0[q], i1[q] - i0[q]);
 #endif
@@ -1669,7 +1695,6 @@ __device__ ROUND_FN void init_round_masked(const Dev& D, Cta& B, uint32_t gwarp,
   const unsigned lane = lane_id();
   const uint32_t n = D.n;
   const bool w4 = (D.flags & F_AC4_POSSIBLE) != 0;
-  const bool w6 = (D.flags & (F_AC6_POSSIBLE | F_AC3_POSSIBLE)) != 0;
   const bool rows = D.ioff != nullptr;
   for (uint32_t base = gwarp * 32u; base < n; base += nwarps * 32u) {
     const uint32_t v = base + lane;
@@ -1694,9 +1719,20 @@ __device__ ROUND_FN void init_round_masked(const Dev& D, Cta& B, uint32_t gwarp,
       big &= big - 1u;
       const uint32_t sj = __shfl_sync(FULL, s, j), dj = __shfl_sync(FULL, d, j);
       uint32_t part = 0;
-      for (uint32_t k0 = 0; k0 < dj; k0 += 32u) {  // warp-uniform
-        const uint32_t k = k0 + lane;
-        part += (k < dj && D.mask[__ldg(&D.tgt[sj + k])] == 0) ? 1u : 0u;
+      // 128 entries per step, four loads in flight per lane; only a run
+      // without AC-4 stops early (the vote would serialise the AC-4 count)
+      for (uint32_t k0 = 0; k0 < dj; k0 += 128u) {  // warp-uniform
+        uint32_t t[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t k = k0 + (uint32_t)q * 32u + lane;
+          t[q] = k < dj ? __ldg(&D.tgt[sj + k]) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t k = k0 + (uint32_t)q * 32u + lane;
+          part += (k < dj && D.mask[t[q]] == 0) ? 1u : 0u;
+        }
         if (!w4 && __any_sync(FULL, part != 0u)) break;
       }
       part = __reduce_add_sync(FULL, part);
@@ -1705,7 +1741,6 @@ __device__ ROUND_FN void init_round_masked(const Dev& D, Cta& B, uint32_t gwarp,
     if (has) {
       D.level[v] = (masked || c == 0u) ? 0u : LIVE;
       if (w4) D.cnt[v] = masked ? 0u : c;
-      if (w6) D.supp[v] = 0u;
     }
     append_dead(D, B, has && !masked && c == 0u, v, 0u, D.live0, true, true, i0, i1 - i0);
   }
@@ -1736,6 +1771,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     S.m_live = D.m;
     for (int i = 0; i < NFEAT; ++i) S.feat[i] = 0.0f;
     S.skew = 0;
+    S.supp_valid = 0;
     S.lround = 0;
     S.lbase[0] = S.lbase[1] = 0;
 

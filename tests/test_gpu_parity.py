@@ -369,6 +369,24 @@ def _commit_segments(alpha, K, P0):
         p *= 2
 
 
+def test_targets_at_any_alignment():
+    """Device CSR arrays that start 4, 8 or 12 bytes past a 16-byte boundary
+    (the scans load four targets at once only where the address allows it)."""
+    import torch
+    P = _P()
+    g = cfg.config_small(1)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    for shift in (1, 2, 3):
+        buf = torch.zeros(g.m + 8, dtype=torch.int32, device="cuda")
+        tgt = buf[shift:shift + g.m]
+        tgt.copy_(torch.from_numpy(g.tgt.astype(np.int32)))
+        off = torch.from_numpy(g.off.astype(np.int32)).cuda()
+        assert tgt.data_ptr() % 16 != 0
+        with P.Trimmer(off, tgt) as t:
+            for v in ["ac6", "ac3", "ac4"]:
+                check(t, lvl, st, alpha, f"{v}-shift{shift}", t.run(v))
+
+
 def test_random_graphs_with_duplicates_and_loops():
     P = _P()
     rng = np.random.default_rng(11)
