@@ -372,18 +372,15 @@ def time_variant(P, t, variant, steps, warmup, flush_buf, graph_off=None):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     last = None
-    # a scheduled variant runs as segments (trim_run: the host hands the run
-    # between single-variant kernels), a fixed one as one asynchronous launch
-    segmented = variant in ("heuristic", "learned", "scripted")
+    # every schedule is enqueued asynchronously: a fixed variant as one
+    # persistent launch, a scheduled one as its first kernel plus the
+    # all-variant continuation behind it; a batched run through trim_batch_run
     launches = 0
     for _ in range(steps):
         flush_buf.add_(1)  # writes more than the L2 holds, on the same stream
         e0.record(stream)
         if run:
             last = run()
-            e1.record(stream)
-        elif segmented:
-            last = t.run(variant)
             e1.record(stream)
         else:
             t.run_async(variant)
@@ -392,7 +389,7 @@ def time_variant(P, t, variant, steps, warmup, flush_buf, graph_off=None):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
         kern.append(last["device_ms"])
-        launches += 1 + last["segments"]  # control-block reset + persistent kernel(s)
+        launches += last["launches"]  # reset, persistent kernel(s), continuation
     last = dict(last, launches=launches)
     return times, kern, last
 
@@ -748,8 +745,9 @@ def run_ours(args, rank, ws, local):
                    "params": tuned or "library defaults",
                    "l2": "flushed before every step (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
-                   "timing": "CUDA events on the library stream around reset + persistent "
-                             "kernel(s) (a scheduled run: all its segments)"},
+                   "timing": "CUDA events on the library stream around trim_run_async: reset "
+                             "+ persistent kernel (a scheduled run: its first kernel + the "
+                             "all-variant continuation behind it)"},
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": st["launches"],

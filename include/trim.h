@@ -106,14 +106,14 @@ typedef struct {
 typedef struct {
   uint32_t block_threads;     /* threads per CTA of the persistent kernel (128..512, x32)  */
   uint32_t ctas_per_sm;       /* persistent CTAs per SM (0 = as many as fit)               */
-  uint32_t sched_commit_rounds; /* HEURISTIC / LEARNED trim_run: after this many rounds
-                                 in a row with the same choice, the run commits to that
-                                 variant and continues on its single-variant kernel, with
-                                 no feature or scheduling work (0 = never commit)        */
+  uint32_t sched_commit_rounds; /* HEURISTIC / LEARNED: after this many rounds in a row
+                                 with the same choice, the run commits to that variant:
+                                 the following rounds run it without consulting the
+                                 scheduler or gathering its features (0 = never commit) */
   uint32_t sched_recheck_rounds; /* ... a committed stretch lasts this many rounds, then the
-                                 scheduler is consulted again for one round (keeping the
-                                 variant re-commits at once); each stretch that ends in
-                                 the same commit doubles the next one                    */
+                                 scheduler is consulted again (keeping the variant
+                                 re-commits at once); each stretch that ends in the same
+                                 commit doubles the next one                             */
   uint64_t spin_limit_ns;     /* bound of every device-side wait; past it the run stops
                                  with TRIM_ERR_TIMEOUT                                       */
   float heur_push_ratio;      /* heuristic: push while sum(indeg F) < ratio * n_live        */
@@ -125,7 +125,28 @@ typedef struct {
                                  next round, and a round ends at one barrier that carries
                                  its totals; a round whose removals overflow the queues
                                  returns to ordinary rounds (0 = never local)            */
+  float sched_commit_confidence; /* LEARNED: a choice whose softmax probability (among the
+                                 variants the run can use) is at least this commits the
+                                 run at once, as sched_commit_rounds unchanged choices do
+                                 (0 = commit only after sched_commit_rounds)              */
+  uint32_t sched_handover;    /* which kernels a scheduled run (trim_run, trim_run_async,
+                                 trim_batch_run) uses, and who passes the run between
+                                 them when the scheduler picks a variant the running
+                                 kernel lacks: TRIM_HANDOVER_*                           */
 } trim_params_t;
+
+/* trim_params_t.sched_handover */
+#define TRIM_HANDOVER_DEVICE 0u /* the run starts on the kernel holding the schedulers and
+                                   the variant the mode's last run on this context chose
+                                   for round 1 (AC-4 with G^T, else AC-3, the first time);
+                                   the kernel holding all three variants is enqueued
+                                   behind it and finishes the run if the first kernel
+                                   handed it over, or returns at once: no host step      */
+#define TRIM_HANDOVER_HOST 1u   /* every segment runs a kernel holding one variant plus the
+                                   schedulers; the host reads the control block after each
+                                   and launches the next (trim_run_async: as _NONE)      */
+#define TRIM_HANDOVER_NONE 2u   /* one launch of the kernel holding all three variants and
+                                   the schedulers                                        */
 
 /* Statistics of the last run (sizes in vertices/edges, times in ms). */
 typedef struct {
@@ -140,6 +161,8 @@ typedef struct {
   uint32_t segments;        /* persistent-kernel launches of the run (1 unless a scheduled
                                trim_run switched between variant kernels)               */
   uint32_t local_rounds;    /* AC-4 rounds that ran CTA-locally (see local_round_edges)   */
+  uint32_t launches;        /* kernel launches of the run: the control-block reset, every
+                               segment, a continuation launch, a dead-mask pass          */
 } trim_run_stats_t;
 
 /* One record per round of a TRIM_FLAG_ROUND_LOG run. features[] are the
@@ -180,12 +203,18 @@ trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void
 /* Runs the whole trimming (all rounds) with the given variant or scheduler.
  * Returns once status/level are final on the device. stats may be NULL.
  * A fixed variant runs as one persistent launch of a kernel that holds only that
- * variant. A scheduled run (HEURISTIC, LEARNED, SCRIPTED) runs as segments: each
- * one launch of the kernel that holds one variant plus the schedulers; when the
- * scheduler picks another variant the kernel saves the schedule state and exits,
- * and the next segment resumes at the same round (the host waits between
- * segments). The result is the same as that of the single all-variant launch
- * that trim_run_async uses. */
+ * variant. A scheduled run (HEURISTIC, LEARNED, SCRIPTED) runs on kernels that
+ * hold the schedulers: when the scheduler picks a variant the running kernel
+ * lacks, the kernel saves the schedule state and exits, and the next launch
+ * resumes at the same round; params.sched_handover says which kernels and who
+ * starts the next one (by default no host step at all). Once the scheduler
+ * commits (sched_commit_rounds, sched_commit_confidence) the committed rounds
+ * skip it inside the same kernel. When the scheduler's only decision of a run
+ * (the one before round 1) committed it to one variant for all its rounds, the
+ * mode's next run on this context runs that variant's single-variant kernel
+ * directly (with TRIM_HANDOVER_DEVICE or _HOST): that decision depends only on
+ * the graph, dead mask, model and parameters, and changing any of them clears
+ * it. Every schedule and handover yields the same status and level. */
 trim_err_t trim_run(trim_ctx* ctx, trim_variant_t variant, trim_run_stats_t* stats);
 
 /* ---- Implicit graphs (Section 2.1, "On-the-fly Property") ----
@@ -297,9 +326,11 @@ trim_err_t trim_set_dead_mask(trim_ctx* ctx, const uint8_t* mask, int on_device)
 trim_err_t trim_run_inout(trim_ctx* ctx, trim_run_stats_t* stats);
 
 /* Enqueues the same work as trim_run without waiting (no host synchronisation,
- * so it may be captured into a CUDA graph): one persistent launch, for a
- * scheduled run that of the kernel holding all three variants. Errors raised on the device surface
- * at the next trim_sync(). */
+ * so it may be captured into a CUDA graph): a fixed variant is one persistent
+ * launch; a scheduled run is the launches of TRIM_HANDOVER_DEVICE (a first
+ * segment and the continuation behind it), or with TRIM_HANDOVER_HOST or _NONE
+ * one launch of the kernel holding all three variants. Errors raised on the
+ * device surface at the next trim_sync(). */
 trim_err_t trim_run_async(trim_ctx* ctx, trim_variant_t variant);
 /* Waits for the enqueued work and reports its device-side status; stats may be NULL. */
 trim_err_t trim_sync(trim_ctx* ctx, trim_run_stats_t* stats);
@@ -325,7 +356,7 @@ trim_err_t trim_level_device_ptr(const trim_ctx* ctx, const uint32_t** out);
  * graphs, so all of them are trimmed together: every round serves every graph
  * still peeling. A fixed variant is one persistent launch, captured into a
  * CUDA graph on the second call with the same variant and replayed from then
- * on; a scheduled variant runs as trim_run runs it (segments). Results equal
+ * on; a scheduled variant runs as trim_run runs it. Results equal
  * trimming each graph alone: read them with trim_status / trim_level. */
 trim_err_t trim_batch_run(trim_ctx* ctx, const uint32_t* graph_off, uint32_t G,
                           trim_variant_t variant, trim_run_stats_t* stats);

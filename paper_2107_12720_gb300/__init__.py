@@ -17,7 +17,8 @@ import numpy as np
 
 from .abi import (LIB_PATH, TRIM_MASKED, TRIM_AC3_PULL, TRIM_AC4_PUSH, TRIM_AC6_SUPPORT, TRIM_FLAG_ROUND_LOG,
                   TRIM_FLAG_STATS, TRIM_FLAG_VALIDATE, TRIM_LIVE, TRIM_MEM_DEVICE, TRIM_MEM_HOST,
-                  TRIM_MEM_HOST_MAPPED, TRIM_MLP_NBLOB,
+                  TRIM_MEM_HOST_MAPPED, TRIM_MLP_NBLOB, TRIM_HANDOVER_DEVICE, TRIM_HANDOVER_HOST,
+                  TRIM_HANDOVER_NONE,
                   TRIM_MLP_NPARAMS, TRIM_SCHED_HEURISTIC, TRIM_SCHED_LEARNED,
                   TRIM_SCHED_SCRIPTED, TrimCsr, TrimError, TrimImplicitGraph, TrimParams,
                   TrimRoundRec,
@@ -232,4 +233,4 @@ def _stats_dict(s: TrimRunStats) -> dict:
             "edges_inspected": s.edges_inspected, "in_edges_pushed": s.in_edges_pushed,
             "candidates": s.candidates, "live_swept": s.live_swept,
             "rounds_by_variant": list(s.rounds_by_variant), "segments": s.segments,
-            "local_rounds": s.local_rounds}
+            "local_rounds": s.local_rounds, "launches": s.launches}

@@ -19,6 +19,7 @@ TRIM_AC4_PUSH, TRIM_AC6_SUPPORT, TRIM_AC3_PULL = 0, 1, 2
 TRIM_SCHED_HEURISTIC, TRIM_SCHED_LEARNED, TRIM_SCHED_SCRIPTED = 3, 4, 5
 TRIM_FLAG_VALIDATE, TRIM_FLAG_STATS, TRIM_FLAG_ROUND_LOG = 1, 2, 4
 TRIM_MEM_HOST, TRIM_MEM_DEVICE, TRIM_MEM_HOST_MAPPED = 0, 1, 2
+TRIM_HANDOVER_DEVICE, TRIM_HANDOVER_HOST, TRIM_HANDOVER_NONE = 0, 1, 2
 TRIM_MLP_NIN, TRIM_MLP_NH, TRIM_MLP_NOUT = 12, 32, 3
 TRIM_MLP_NPARAMS = 1571
 TRIM_MLP_NBLOB = TRIM_MLP_NPARAMS + 4 * TRIM_MLP_NIN
@@ -42,7 +43,8 @@ class TrimParams(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("sched_commit_rounds", ctypes.c_uint32), ("sched_recheck_rounds", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("heur_push_ratio", ctypes.c_float),
-                ("heur_ac6_ratio", ctypes.c_float), ("local_round_edges", ctypes.c_uint32)]
+                ("heur_ac6_ratio", ctypes.c_float), ("local_round_edges", ctypes.c_uint32),
+                ("sched_commit_confidence", ctypes.c_float), ("sched_handover", ctypes.c_uint32)]
 
 
 class TrimImplicitGraph(ctypes.Structure):
@@ -62,7 +64,8 @@ class TrimRunStats(ctypes.Structure):
                 ("device_ms", ctypes.c_float), ("edges_inspected", ctypes.c_uint64),
                 ("in_edges_pushed", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("live_swept", ctypes.c_uint64), ("rounds_by_variant", ctypes.c_uint32 * 3),
-                ("segments", ctypes.c_uint32), ("local_rounds", ctypes.c_uint32)]
+                ("segments", ctypes.c_uint32), ("local_rounds", ctypes.c_uint32),
+                ("launches", ctypes.c_uint32)]
 
 
 class TrimRoundRec(ctypes.Structure):

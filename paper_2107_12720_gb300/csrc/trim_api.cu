@@ -69,7 +69,13 @@ struct trim_ctx {
   int grids[10] = {};  // cooperative grid size of each kernel flavour
   trimk::Dev last_dev{};        // arguments of the last launch (segments reuse them)
   int seg_first[3] = {-1, -1, -1};  // per scheduled mode: flavour of its last first round
-  uint64_t last_segments = 0;       // kernel launches of the last trim_run
+  uint64_t last_segments = 0;       // segments of the last trim_run
+  uint64_t last_launches = 0;       // kernel launches of the last trim_run
+  int cont_mode = -1;               // the pending run has a continuation launch: its mode
+  int sched_mode = -1;              // the pending run is scheduled: its mode
+  // per scheduled mode: the variant of its last run on this context if that
+  // run's only scheduler decision (before round 1) committed it for good
+  int seg_whole[3] = {-1, -1, -1};
   std::vector<uint8_t> h_script;    // host copy of the scripted schedule
   cudaGraphExec_t batch_exec = nullptr;  // captured batched launch (trim_batch_run)
   cudaStream_t cap_stream = nullptr;      // private stream used only for that capture
@@ -89,6 +95,13 @@ namespace {
 trim_err_t fail(trim_ctx* c, trim_err_t code, const std::string& msg) {
   if (c) c->err = msg; else g_create_error = msg;
   return code;
+}
+
+// The graph, its dead mask, the model or the parameters changed: a scheduled
+// run's round-1 choice may differ from the one its last run made.
+void forget_first_flavours(trim_ctx* c) {
+  c->seg_first[0] = c->seg_first[1] = c->seg_first[2] = -1;
+  c->seg_whole[0] = c->seg_whole[1] = c->seg_whole[2] = -1;
 }
 
 trim_err_t cuda_fail(trim_ctx* c, cudaError_t e, const char* what) {
@@ -247,6 +260,8 @@ void default_params(trim_params_t* p) {
   p->heur_push_ratio = 1.0f;
   p->heur_ac6_ratio = 1.0f;
   p->local_round_edges = 1u << 18;
+  p->sched_commit_confidence = 0.9f;
+  p->sched_handover = TRIM_HANDOVER_DEVICE;
 }
 
 // per-warp append slices in dynamic shared memory: 4 buffers (dead log, AC-4
@@ -361,6 +376,7 @@ trim_err_t build_transpose(trim_ctx* c) {
   }
   TRY(sync_check(c));
   c->ioff = ioff;
+  forget_first_flavours(c);
   c->itgt = itgt;
   return TRIM_OK;
 }
@@ -634,10 +650,13 @@ trim_err_t ensure_inout(trim_ctx* c) {
 }
 
 // Enqueues one run. A scheduled variant runs on the all-variant kernel, or with
-// seg_flavour >= 0 as the first segment of a segmented run (run_segmented).
-// With inout, the run is in+out trimming (variant must be TRIM_AC4_PUSH).
+// seg_flavour >= 0 on that flavour as the first segment: followed, with cont,
+// by a continuation launch of the all-variant kernel (which finishes the run
+// if the first segment handed it over), else by host-side segments
+// (run_segmented). With inout, the run is in+out trimming (variant must be
+// TRIM_AC4_PUSH).
 trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1,
-                       uint32_t commit_after = 0, bool inout = false) {
+                       uint32_t commit_after = 0, bool inout = false, bool cont = false) {
   if ((int)variant < 0 || variant > TRIM_SCHED_SCRIPTED)
     return fail(c, TRIM_ERR_INVALID_ARG, "unknown variant");
   if (c->implicit) {
@@ -680,6 +699,9 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   if (ac4) { f |= trimk::F_AC4_POSSIBLE; TRY(ensure_work_list(c)); }
   if (ac6) f |= trimk::F_AC6_POSSIBLE;
   if (ac3) f |= trimk::F_AC3_POSSIBLE;
+  c->cont_mode = -1;
+  c->sched_mode = (variant >= TRIM_SCHED_HEURISTIC) ? (int)variant : -1;
+  c->last_launches = 0;
   if (c->n == 0) {
     c->ran = true;
     c->pending = false;
@@ -714,10 +736,12 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   D.heur_push_ratio = c->params.heur_push_ratio;
   D.heur_ac6_ratio = c->params.heur_ac6_ratio;
   D.commit_after = commit_after;
-  D.stop_round = 0;
+  D.commit_confidence = c->params.sched_commit_confidence;
+  D.recheck_rounds = c->params.sched_recheck_rounds;
   D.local_edges_max = c->params.local_round_edges;
-  // segmented scheduled runs keep the live-edge count through lean stretches
-  if (variant >= TRIM_SCHED_HEURISTIC && seg_flavour >= 0) D.flags |= trimk::F_LIVE_EDGES;
+  // scheduled runs keep the live-edge count (a feature); with G^T and AC-4 the
+  // scheduler kernels derive it from running totals instead
+  if (variant >= TRIM_SCHED_HEURISTIC && !(ac4 && c->ioff)) D.flags |= trimk::F_LIVE_EDGES;
   // a fixed variant runs on its lean single-variant flavour
   int flavour = kFlavourAll;
   if (c->implicit) flavour = variant == TRIM_AC6_SUPPORT ? kFlavourImplicitAC6 : kFlavourImplicitAC3;
@@ -727,6 +751,7 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   c->last_dev = D;
   const int grid = c->grids[flavour];
   if ((uint32_t)grid > 8192) return fail(c, TRIM_ERR_INVALID_ARG, "grid too large");
+  c->last_launches = 2;  // control-block reset + persistent kernel
   trim_reset_ctrl_kernel<<<1, 32, 0, c->stream>>>(c->ctrl);
   CK(cudaGetLastError());
   // device_ms covers the persistent kernel alone; inside a stream capture the
@@ -738,6 +763,19 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
                                  dim3(c->params.block_threads), args,
                                  dyn_smem_bytes(c->params.block_threads),
                                  c->stream));
+  if (cont) {
+    // the all-variant kernel finishes the run if the first segment handed it
+    // over (its scheduler chose a variant that kernel lacks); else it returns
+    // at once
+    Dev Dc = D;
+    Dc.flags |= trimk::F_CONTINUE;
+    void* cargs[] = {&Dc};
+    CK(cudaLaunchCooperativeKernel((const void*)kFlavours[kFlavourAll],
+                                   dim3(c->grids[kFlavourAll]), dim3(c->params.block_threads),
+                                   cargs, dyn_smem_bytes(c->params.block_threads), c->stream));
+    c->cont_mode = (int)variant;
+    c->last_launches = 3;
+  }
   CK(cudaEventRecordWithFlags(c->ev1, c->stream, rec));
   c->pending = true;
   c->ran = false;
@@ -916,16 +954,12 @@ trim_err_t run_scc(trim_ctx* c, uint32_t* out, int out_on_device, trim_scc_stats
   return TRIM_OK;
 }
 
-// Launches the next segment of a segmented run, resuming from the schedule
-// state the last segment saved: `flavour` runs with `mode` (the scheduled mode,
-// or a fixed variant for a committed stretch that hands back at stop_round).
-trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base, uint32_t mode,
-                          uint32_t stop_round) {
+// Launches the next segment of a host-segmented run: `flavour` resumes the run
+// from the schedule state the last segment saved.
+trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base) {
   trimk::Dev D = c->last_dev;
   D.resume = 1;
   D.bar_base = bar_base;
-  D.mode = mode;
-  D.stop_round = stop_round;
   void* args[] = {&D};
   CK(cudaLaunchCooperativeKernel((const void*)kFlavours[flavour], dim3(c->grids[flavour]),
                                  dim3(c->params.block_threads), args,
@@ -935,33 +969,34 @@ trim_err_t launch_segment(trim_ctx* c, int flavour, uint32_t bar_base, uint32_t 
   return TRIM_OK;
 }
 
+// The first segment's commit length of a scheduled mode (a scripted run never
+// commits: its script decides every round).
+uint32_t commit_rounds(const trim_ctx* c, trim_variant_t variant) {
+  return variant == TRIM_SCHED_SCRIPTED ? 0u : c->params.sched_commit_rounds;
+}
 
-// A scheduled run (heuristic, learned, scripted) on the lean kernels: each
-// segment is one cooperative launch. The scheduler runs on the flavour that
-// holds one variant plus the schedulers; when it picks a variant the running
-// kernel lacks, the kernel saves the schedule state and exits, and the host
-// launches the flavour of that variant, which resumes at the same round. When
-// the heuristic or learned scheduler has kept its choice for
-// sched_commit_rounds rounds, the run commits: the next segment is the
-// single-variant kernel of that variant (no features, no scheduling) for
-// sched_recheck_rounds rounds, after which the scheduler is consulted again
-// for one round (if it keeps the variant, the run re-commits at once); a
-// stretch that ends in the same commit doubles the next one. The first
-// segment starts on the flavour this mode's last run started with.
+// The kernel flavour a scheduled mode's run starts on: the one with the
+// schedulers and the variant its last run chose for round 1 (a scripted run:
+// its first entry; else AC-4 with G^T, AC-3 without).
+int first_flavour(const trim_ctx* c, trim_variant_t variant) {
+  const int mi = (int)variant - (int)TRIM_SCHED_HEURISTIC;
+  if (c->seg_first[mi] >= 0) return c->seg_first[mi];
+  if (variant == TRIM_SCHED_SCRIPTED && !c->h_script.empty())
+    return kFlavourSeg + std::min<int>(c->h_script[0], TRIM_AC3_PULL);
+  return kFlavourSeg + (c->ioff ? TRIM_AC4_PUSH : TRIM_AC3_PULL);
+}
+
+// A scheduled run (heuristic, learned, scripted) with host-side handover: each
+// segment is one launch of a kernel that holds one variant plus the
+// schedulers; when the scheduler picks a variant the running kernel lacks,
+// the kernel saves the schedule state and exits, and the host launches the
+// kernel of that variant, which resumes at the same round. Commits stay
+// inside a kernel (a committed stretch skips the scheduler).
 trim_err_t run_segmented(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats) {
   const int mi = (int)variant - (int)TRIM_SCHED_HEURISTIC;
-  int first = c->seg_first[mi];
-  if (first < 0 && variant == TRIM_SCHED_SCRIPTED && !c->h_script.empty())
-    first = kFlavourSeg + std::min<int>(c->h_script[0], TRIM_AC3_PULL);
-  if (first < 0) first = kFlavourSeg + (c->ioff ? TRIM_AC4_PUSH : TRIM_AC3_PULL);
-  const uint32_t commit_after =
-      variant == TRIM_SCHED_SCRIPTED ? 0u : c->params.sched_commit_rounds;
-  TRY(enqueue_run(c, variant, first, commit_after));
+  TRY(enqueue_run(c, variant, first_flavour(c, variant), commit_rounds(c, variant)));
   if (!c->pending) return finish_run(c, stats);
   uint64_t segments = 1;
-  uint64_t period = std::max<uint32_t>(1u, c->params.sched_recheck_rounds);
-  int last_commit = -1;
-  bool lean = false;  // the last segment was a committed single-variant stretch
   while (true) {
     TRY(read_ctrl(c));
     const Ctrl& h = *c->h_ctrl;
@@ -971,24 +1006,34 @@ trim_err_t run_segmented(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* 
       c->s_cnt_dirty = true;
       return fail(c, TRIM_ERR_STATE, "invalid segment handover");
     }
-    const uint32_t v = h.resume_variant, round = h.saved.round;
-    if (h.commit) {
-      period = ((int)v == last_commit) ? std::min<uint64_t>(period * 2, 1u << 30)
-                                       : std::max<uint32_t>(1u, c->params.sched_recheck_rounds);
-      last_commit = (int)v;
-      const uint64_t stop = std::min<uint64_t>((uint64_t)round + period, 0xFFFFFFFFull);
-      TRY(launch_segment(c, (int)v, h.bar, v, (uint32_t)stop));
-      lean = true;
-    } else {
-      // a committed stretch reached its end, or the scheduler picked a
-      // variant the running kernel lacks: the scheduler flavour of v resumes
-      if (!lean && round == 1) c->seg_first[mi] = kFlavourSeg + (int)v;
-      TRY(launch_segment(c, kFlavourSeg + (int)v, h.bar, (uint32_t)variant, 0u));
-      lean = false;
-    }
+    const uint32_t v = h.resume_variant;
+    if (segments == 2 && h.saved.round == 1) c->seg_first[mi] = kFlavourSeg + (int)v;
+    TRY(launch_segment(c, kFlavourSeg + (int)v, h.bar));
   }
   c->last_segments = segments;
+  c->last_launches = 1 + segments;
   return finish_run(c, stats, true);
+}
+
+// A scheduled run, with the kernels and handover params.sched_handover names;
+// waits for it.
+trim_err_t run_scheduled(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats) {
+  const int whole = c->seg_whole[(int)variant - (int)TRIM_SCHED_HEURISTIC];
+  if (whole >= 0 && c->params.sched_handover != TRIM_HANDOVER_NONE) {
+    TRY(enqueue_run(c, (trim_variant_t)whole));  // the schedule is known: one variant
+    return finish_run(c, stats);
+  }
+  switch (c->params.sched_handover) {
+    case TRIM_HANDOVER_HOST:
+      return run_segmented(c, variant, stats);
+    case TRIM_HANDOVER_NONE:
+      TRY(enqueue_run(c, variant, -1, commit_rounds(c, variant)));
+      return finish_run(c, stats);
+    default:
+      TRY(enqueue_run(c, variant, first_flavour(c, variant), commit_rounds(c, variant), false,
+                      true));
+      return finish_run(c, stats);
+  }
 }
 
 // Waits for the enqueued run and publishes its statistics (ctrl_read: the
@@ -1011,6 +1056,28 @@ trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read) {
       CK(cudaGetLastError());
       TRY(sync_check(c));
     }
+    uint64_t launches = c->last_launches;
+    if (c->cont_mode >= 0) {  // first segment + continuation: what ran, as counted
+      c->last_segments = h.segments;
+      // the next run of this mode starts on the kernel of round 1's variant
+      if (h.first_exit_round == 1 && h.resume_variant <= TRIM_AC3_PULL)
+        c->seg_first[c->cont_mode - (int)TRIM_SCHED_HEURISTIC] =
+            kFlavourSeg + (int)h.resume_variant;
+      c->cont_mode = -1;
+    }
+    if (c->sched_mode >= 0) {
+      // a run whose only scheduler decision, before round 1, committed it to
+      // one variant for all its rounds: that decision depends only on the
+      // graph, mask, model and parameters, so the mode's next run on this
+      // context is the same single-variant run
+      int v = -1, used = 0;
+      for (int i = 0; i < 3; ++i)
+        if (h.vcount[i]) v = i, ++used;
+      c->seg_whole[c->sched_mode - (int)TRIM_SCHED_HEURISTIC] =
+          (h.consults == 1 && h.commit_round0 && h.first_exit_round == 0 && used == 1) ? v : -1;
+      c->sched_mode = -1;
+    }
+    if (c->has_mask && c->n) launches += 1;
     trim_run_stats_t s{};
     s.rounds = h.rounds;
     s.n_dead = h.n_dead;
@@ -1024,6 +1091,7 @@ trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read) {
     for (int i = 0; i < 3; ++i) s.rounds_by_variant[i] = h.vcount[i];
     s.segments = (uint32_t)c->last_segments;
     s.local_rounds = h.local_rounds;
+    s.launches = (uint32_t)std::min<uint64_t>(launches, 0xFFFFFFFFu);
     c->last = s;
     c->ran = true;
   }
@@ -1105,6 +1173,8 @@ trim_err_t enqueue_batch(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
     c->batch_variant = (int)variant;
   }
   CK(cudaGraphLaunch(c->batch_exec, c->stream));
+  c->cont_mode = -1;
+  c->last_launches = 2;  // the replayed reset + persistent kernel
   c->pending = true;
   c->ran = false;
   return TRIM_OK;
@@ -1156,7 +1226,7 @@ trim_err_t trim_run(trim_ctx* c, trim_variant_t variant, trim_run_stats_t* stats
   if (c->implicit && variant != TRIM_AC6_SUPPORT && variant != TRIM_AC3_PULL)
     return fail(c, TRIM_ERR_INVALID_ARG, "an implicit graph runs TRIM_AC6_SUPPORT or TRIM_AC3_PULL only");
   if (variant >= TRIM_SCHED_HEURISTIC && variant <= TRIM_SCHED_SCRIPTED)
-    return run_segmented(c, variant, stats);
+    return run_scheduled(c, variant, stats);
   TRY(enqueue_run(c, variant));
   return finish_run(c, stats);
 }
@@ -1177,6 +1247,15 @@ trim_err_t trim_run_scc(trim_ctx* c, uint32_t* comp, int out_on_device, trim_scc
 trim_err_t trim_run_async(trim_ctx* c, trim_variant_t variant) {
   if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
   c->last_segments = 1;
+  if (variant >= TRIM_SCHED_HEURISTIC && variant <= TRIM_SCHED_SCRIPTED && !c->implicit) {
+    const int whole = c->seg_whole[(int)variant - (int)TRIM_SCHED_HEURISTIC];
+    if (whole >= 0 && c->params.sched_handover == TRIM_HANDOVER_DEVICE)
+      return enqueue_run(c, (trim_variant_t)whole);  // the schedule is known: one variant
+    if (c->params.sched_handover == TRIM_HANDOVER_DEVICE)
+      return enqueue_run(c, variant, first_flavour(c, variant), commit_rounds(c, variant), false,
+                         true);
+    return enqueue_run(c, variant, -1, commit_rounds(c, variant));
+  }
   return enqueue_run(c, variant);
 }
 
@@ -1196,10 +1275,10 @@ trim_err_t trim_batch_run(trim_ctx* c, const uint32_t* graph_off, uint32_t G,
       return fail(c, TRIM_ERR_INVALID_ARG, "graph_off must be non-decreasing");
   if (c->flags & TRIM_FLAG_VALIDATE) TRY(validate_batch(c, graph_off, G));
   c->last_segments = 1;
-  // a scheduled variant hands the run between kernels from the host
-  // (segments), which a captured graph cannot do: it runs as trim_run does
+  // a scheduled variant runs as trim_run runs it (its first kernel depends on
+  // the mode's last run: nothing is captured)
   if (variant >= TRIM_SCHED_HEURISTIC && variant <= TRIM_SCHED_SCRIPTED)
-    return run_segmented(c, variant, stats);
+    return run_scheduled(c, variant, stats);
   TRY(enqueue_batch(c, graph_off, G, variant));
   return finish_run(c, stats);
 }
@@ -1265,7 +1344,12 @@ trim_err_t trim_set_params(trim_ctx* c, const trim_params_t* p) {
     return fail(c, TRIM_ERR_INVALID_ARG, "heuristic ratios must be > 0");
   if (p->sched_commit_rounds && !p->sched_recheck_rounds)
     return fail(c, TRIM_ERR_INVALID_ARG, "sched_recheck_rounds must be > 0 when committing");
+  if (!(p->sched_commit_confidence >= 0.0f && p->sched_commit_confidence <= 1.0f))
+    return fail(c, TRIM_ERR_INVALID_ARG, "sched_commit_confidence must be in [0, 1]");
+  if (p->sched_handover > TRIM_HANDOVER_NONE)
+    return fail(c, TRIM_ERR_INVALID_ARG, "unknown sched_handover");
   drop_batch_graph(c);
+  forget_first_flavours(c);
   const trim_params_t old = c->params;
   c->params = *p;
   trim_err_t e = compute_grid(c);
@@ -1285,6 +1369,7 @@ trim_err_t trim_get_params(const trim_ctx* c, trim_params_t* p) {
 
 trim_err_t trim_set_model(trim_ctx* c, const float* blob, size_t n_floats) {
   if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
+  forget_first_flavours(c);
   if (blob == nullptr) {
     drop_batch_graph(c);
     c->has_model = false;
@@ -1304,6 +1389,7 @@ trim_err_t trim_set_dead_mask(trim_ctx* c, const uint8_t* mask, int on_device) {
   if (!c) return fail(nullptr, TRIM_ERR_INVALID_ARG, "null context");
   if (c->pending) TRY(finish_run(c, nullptr));
   drop_batch_graph(c);
+  forget_first_flavours(c);
   if (mask == nullptr) {
     c->has_mask = false;
     return TRIM_OK;
@@ -1331,7 +1417,7 @@ trim_err_t trim_set_schedule(trim_ctx* c, const uint8_t* v, uint32_t len) {
   TRY(sync_check(c));
   c->script_len = len;
   c->h_script.assign(v, v + len);
-  c->seg_first[TRIM_SCHED_SCRIPTED - TRIM_SCHED_HEURISTIC] = -1;
+  forget_first_flavours(c);
   return TRIM_OK;
 }
 

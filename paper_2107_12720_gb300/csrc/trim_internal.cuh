@@ -27,6 +27,7 @@ constexpr uint32_t F_AC4_POSSIBLE = 0x200;   // counters initialised, AC-4 work 
 constexpr uint32_t F_AC6_POSSIBLE = 0x400;
 constexpr uint32_t F_AC3_POSSIBLE = 0x800;
 constexpr uint32_t F_LIVE_EDGES = 0x1000;    // scheduled run: keep the live-edge count in every flavour
+constexpr uint32_t F_CONTINUE = 0x2000;      // continuation launch: resume the run if a segment handed it over
 
 // Per-round accumulators, filled while round r runs (ring slot r & 3). CTA 0
 // zeroes slot (k+2) & 3 at the start of round k: that slot was last read at the
@@ -60,6 +61,12 @@ struct Sched {
   uint32_t mixed;         // 1 once a round ran AC-6 or AC-3 (AC-4 must then re-check levels)
   uint32_t vcount[3];     // rounds run so far by AC-4, AC-6, AC-3
   uint32_t stable;        // rounds in a row the scheduler kept its choice (0 outside schedulers)
+  // committed stretch: rounds r < cstop run the committed variant without
+  // consulting the scheduler (cstop = 0: none); the scheduler is consulted
+  // again after round cstop, whose features it reads
+  uint32_t cstop;
+  uint32_t cperiod;       // length of the last committed stretch
+  uint32_t clast;         // variant of the last commit (NIL: none yet)
   uint32_t bmax;          // largest in-degree among work-list entries AC-4 has not pushed
   unsigned long long m_live;     // out-edges of live vertices
   float feat[12];                // features that chose this round's variant
@@ -102,8 +109,10 @@ struct Ctrl {
   // the schedule state here and exits; the kernel that has it resumes from it
   unsigned int resume;            // 1: a segment ended early, state in `saved`
   unsigned int resume_variant;    // the variant the next segment must run
-  unsigned int segments;          // kernels run so far in this run
-  unsigned int commit;            // 1: the segment ended because the scheduler committed
+  unsigned int segments;          // kernels that ran part of this run
+  unsigned int first_exit_round;  // round at which the first segment handed over (0: never)
+  unsigned int consults;          // rounds whose variant the scheduler chose
+  unsigned int commit_round0;     // 1: round 1's choice committed the run at once
   Sched saved;
 };
 
@@ -146,8 +155,8 @@ struct Dev {
   uint32_t* bsum;     // per-CTA scratch of the grid-wide scan
   uint32_t sbuf_cap;  // entries of each CTA append buffer (dynamic shared memory)
   uint32_t resume;    // 1: continue the run from Ctrl::saved instead of starting it
-  uint32_t stop_round;    // != 0: hand the run back to the host at the start of this round
   uint32_t commit_after;  // != 0: scheduler flavours commit after this many stable rounds
+  uint32_t recheck_rounds;  // length of the first committed stretch (doubles while repeated)
   uint32_t bar_base;  // grid-barrier counter when this kernel starts (0 for a new run)
   uint32_t local_edges_max;  // AC-4: pending in-edges up to which rounds run locally (0: never)
   Ctrl* C;
@@ -161,6 +170,7 @@ struct Dev {
   uint64_t spin_limit_ns;
   float heur_push_ratio;
   float heur_ac6_ratio;
+  float commit_confidence;  // LEARNED: commit at once at this softmax probability (0: never)
 };
 
 // ---------------------------------------------------------------- primitives

@@ -31,9 +31,11 @@
 //
 // A scheduled run may span several launches (segments): at the start of a
 // round every CTA can decide from the same state to stop (the kernel lacks the
-// chosen variant, the scheduler committed to its choice, or the host asked for
-// the run back at that round); CTA 0 then saves the schedule state in the
-// control block, and the next launch resumes from it at the same round.
+// variant the scheduler chose); CTA 0 then saves the schedule state in the
+// control block, and the next launch resumes from it at the same round. A
+// scheduler that commits to its choice stays in the same kernel: the rounds
+// of a committed stretch skip the scheduler and its features (and in the AC-4
+// + schedulers flavour may run as local rounds).
 #include "trim_internal.cuh"
 
 // This file is compiled once per kernel flavour: TRIM_MODES is a bit set of the
@@ -96,7 +98,8 @@ struct WarpSlice {
   uint32_t max_din;          // largest in-degree among this warp's work-list entries
 };
 
-// Local AC-4 rounds (the AC-4-only flavour): while the pending work is small,
+// Local AC-4 rounds (the AC-4-only flavour, and the AC-4 + schedulers flavour
+// inside committed stretches): while the pending work is small,
 // each CTA keeps the vertices it removes in a shared-memory queue together with
 // their predecessors (their G^T rows, loaded when they are removed) and
 // decrements those predecessors' counters itself in the next round. A round then
@@ -104,7 +107,7 @@ struct WarpSlice {
 // reservations, nor a read of the control block: it ends at a barrier that
 // carries the round's totals (see local_barrier). A removal that does not fit
 // the queue goes to the global lists, and the run returns to ordinary rounds.
-#if TRIM_MODES == 1
+#if TRIM_MODES == 1 || TRIM_MODES == 9
 #define TRIM_LOCAL 1
 #else
 #define TRIM_LOCAL 0
@@ -117,13 +120,13 @@ constexpr uint32_t LQ_DMAX = 64;      // larger in-degrees always go to the glob
 
 // Per-CTA shared state.
 struct Cta {
-#if TRIM_MODES & 8
-  float model[TRIM_MLP_NBLOB];  // scheduler MLP (copied once per launch)
-#endif
   Sched S;
   WarpSlice ws[MAX_WARPS];
   unsigned epoch;     // grid barriers passed by this kernel
   unsigned bar_base;  // barrier counter when this kernel started
+  unsigned resume;    // this launch continues a run a segment handed over
+  unsigned skip;      // continuation launch of a run that needs none: return at once
+  unsigned mode;      // trim_variant_t of the run
   unsigned err;
   unsigned w4_wide;   // initial pass: the work-list slices take all four buffers
   unsigned long long kstat[4];  // TRIM_FLAG_STATS totals of this CTA (see stats_flush)
@@ -142,6 +145,14 @@ struct Cta {
   uint32_t lq_next;                   // how the stretch goes on after the local barrier
 #endif
 };
+
+// Are scheduler features gathered in round S.round? The learned scheduler (and
+// a round log of a scheduled run) reads them after every round in which it is
+// consulted, i.e. every round outside a committed stretch.
+__device__ __forceinline__ bool feats_on(const Dev& D, const Sched& S) {
+  return (MODES & M_SCHED) && (D.flags & F_NEED_FEATURES) &&
+         !(S.cstop != 0u && S.round < S.cstop);
+}
 
 // dynamic shared memory: per warp w, 4 slices of LW words at w * 4 * LW:
 // dead-log entries | work-list rows | work-list edge offsets (warp-local) | live-list entries
@@ -346,7 +357,7 @@ __device__ __forceinline__ void append_dead(const Dev& D, Cta& B, bool pred, uin
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const unsigned mask = __ballot_sync(FULL, pred);
   if (mask == 0u) return;
-  const bool feats = (MODES & M_SCHED) && (D.flags & F_NEED_FEATURES);
+  const bool feats = feats_on(D, B.S);
   const bool live_edges = feats || (D.flags & F_LIVE_EDGES);
   // whenever the run may use AC-4, every flavour keeps its work list complete
   const bool track = D.ioff != nullptr && ((D.flags & F_AC4_POSSIBLE) || feats);
@@ -610,7 +621,8 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
       if (lane == 0) set_error(D, TRIM_ERR_STATE, 0xD6);
       vb = 0xFFFFFFFFu;
     }
-    if (((MODES & M_SCHED) && (D.flags & F_NEED_FEATURES)) || (D.flags & F_LIVE_EDGES)) {
+    const bool feats = feats_on(D, B.S);
+    if (feats || (D.flags & F_LIVE_EDGES)) {
       const uint32_t s_out = __reduce_add_sync(FULL, has ? B.ws[lane].sum_out : 0u);
       if (lane == 4 && s_out) atomicAdd(&rs->sum_out, (unsigned long long)s_out);
     }
@@ -618,7 +630,7 @@ __device__ void flush_round(const Dev& D, Cta& B, uint32_t r, uint32_t* live_out
       const uint32_t md = __reduce_max_sync(FULL, has ? B.ws[lane].max_din : 0u);
       if (lane == 8 && md) atomicMax(&rs->max_din, md);
     }
-    if ((MODES & M_SCHED) && (D.flags & F_NEED_FEATURES)) {
+    if (feats) {
       const uint32_t s_in = __reduce_add_sync(FULL, has ? B.ws[lane].sum_in : 0u);
       uint32_t h[3];
       for (int i = 0; i < 3; ++i) h[i] = __reduce_add_sync(FULL, has ? B.ws[lane].hist[i] : 0u);
@@ -806,42 +818,63 @@ __device__ uint32_t heuristic_choice(const Dev& D, const Sched& L, uint32_t nF, 
   return TRIM_AC3_PULL;
 }
 
-// Warp-collective MLP 12 -> 32 -> 32 -> 3 (ReLU); returns the argmax class
-// among the available variants; *in_range = all features inside [lo, hi].
-// Warp-collective MLP 12 -> 32 -> 32 -> 3 (ReLU) on the shared-memory copy of
-// the model (layers stored transposed so that lane j reads column j without bank
-// conflicts); returns the argmax class among the available variants and
-// whether every feature lies in the model's training range.
-__device__ uint32_t mlp_choice(const Dev& D, const float* B, const float* f, bool* in_range) {
+// Warp-collective MLP 12 -> 32 -> 32 -> 3 (ReLU) read from the model blob in
+// global memory (W1[32][12] b1[32] W2[32][32] b2[32] W3[3][32] b3[3] mean[12]
+// istd[12] lo[12] hi[12]; 16-byte aligned): lane j computes hidden unit j of
+// each layer from row j of W1 and W2 (float4 loads). It runs only in rounds
+// after which the scheduler is consulted, so the model stays out of shared
+// memory. Returns the argmax class among the available variants, its softmax
+// probability, and whether every feature lies in the model's training range.
+__device__ uint32_t mlp_choice(const Dev& D, const float* f, bool* in_range,
+                               float* confidence) {
   const unsigned lane = lane_id();
-  const float *W1t = B, *b1 = B + 384, *W2t = B + 416, *b2 = B + 1440, *W3 = B + 1472,
-              *b3 = B + 1568, *mean = B + 1571, *istd = B + 1583, *lo = B + 1595,
-              *hi = B + 1607;
+  const float* M = D.model;
   bool ok = true;
   float x[NFEAT];
 #pragma unroll
   for (int i = 0; i < NFEAT; ++i) {
-    ok = ok && f[i] >= lo[i] && f[i] <= hi[i];
-    x[i] = (f[i] - mean[i]) * istd[i];
+    const float mean = __ldg(M + 1571 + i), istd = __ldg(M + 1583 + i);
+    const float lo = __ldg(M + 1595 + i), hi = __ldg(M + 1607 + i);
+    ok = ok && f[i] >= lo && f[i] <= hi;
+    x[i] = (f[i] - mean) * istd;
   }
-  float h1 = b1[lane];
+  const float4* w1 = reinterpret_cast<const float4*>(M + lane * NFEAT);
+  float h1 = __ldg(M + 384 + lane);
 #pragma unroll
-  for (int i = 0; i < NFEAT; ++i) h1 = fmaf(W1t[i * 32 + lane], x[i], h1);
+  for (int q = 0; q < NFEAT / 4; ++q) {
+    const float4 w = __ldg(w1 + q);
+    h1 = fmaf(w.x, x[4 * q], h1);
+    h1 = fmaf(w.y, x[4 * q + 1], h1);
+    h1 = fmaf(w.z, x[4 * q + 2], h1);
+    h1 = fmaf(w.w, x[4 * q + 3], h1);
+  }
   h1 = fmaxf(h1, 0.0f);
-  float acc[4] = {b2[lane], 0.0f, 0.0f, 0.0f};  // four chains for instruction-level parallelism
+  const float4* w2 = reinterpret_cast<const float4*>(M + 416 + lane * 32);
+  float acc[4] = {__ldg(M + 1440 + lane), 0.0f, 0.0f, 0.0f};  // four independent chains
 #pragma unroll
-  for (int k = 0; k < 32; ++k)
-    acc[k & 3] = fmaf(W2t[k * 32 + lane], __shfl_sync(FULL, h1, k), acc[k & 3]);
+  for (int q = 0; q < 8; ++q) {
+    const float4 w = __ldg(w2 + q);
+    acc[0] = fmaf(w.x, __shfl_sync(FULL, h1, 4 * q), acc[0]);
+    acc[1] = fmaf(w.y, __shfl_sync(FULL, h1, 4 * q + 1), acc[1]);
+    acc[2] = fmaf(w.z, __shfl_sync(FULL, h1, 4 * q + 2), acc[2]);
+    acc[3] = fmaf(w.w, __shfl_sync(FULL, h1, 4 * q + 3), acc[3]);
+  }
   const float h2 = fmaxf((acc[0] + acc[1]) + (acc[2] + acc[3]), 0.0f);
   float z[3];
 #pragma unroll
-  for (int o = 0; o < 3; ++o) z[o] = warp_sum(W3[o * 32 + lane] * h2) + b3[o];
+  for (int o = 0; o < 3; ++o)
+    z[o] = warp_sum(__ldg(M + 1472 + o * 32 + lane) * h2) + __ldg(M + 1568 + o);
   if (D.ioff == nullptr || !(D.flags & F_AC4_POSSIBLE)) z[TRIM_AC4_PUSH] = -3.0e38f;
   if (!(D.flags & F_AC6_POSSIBLE)) z[TRIM_AC6_SUPPORT] = -3.0e38f;
   if (!(D.flags & F_AC3_POSSIBLE)) z[TRIM_AC3_PULL] = -3.0e38f;
   uint32_t best = 0;
   if (z[1] > z[best]) best = 1;
   if (z[2] > z[best]) best = 2;
+  // softmax probability of the choice among the available variants
+  float den = 0.0f;
+#pragma unroll
+  for (int o = 0; o < 3; ++o) den += expf(z[o] - z[best]);
+  *confidence = 1.0f / den;
   *in_range = ok;
   return best;
 }
@@ -856,7 +889,10 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
   Sched L = B.S;
   const uint32_t r = L.round;
   const RoundStat* rs = &C->rs[r & 3];
-  const bool feats = (MODES & M_SCHED) && (D.flags & F_NEED_FEATURES);
+  // the scheduler chooses round r+1 unless a committed stretch covers it
+  const bool consult = (MODES & M_SCHED) && B.mode > TRIM_AC3_PULL &&
+                       !(L.cstop != 0u && r < L.cstop);
+  const bool feats = feats_on(D, L);
   const bool logged = (D.flags & F_ROUND_LOG) && D.rlog != nullptr && r >= 1 && r - 1 < D.rlog_cap;
   // every value this step reads from the control block, issued together
   const uint32_t err = ld_relaxed(&C->err);
@@ -868,10 +904,12 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
   unsigned long long sum_in = 0, sum_out = 0, t_r = 0, t_rm1 = 0, local_edges = 0;
   uint32_t h0 = 0, h1 = 0, h2 = 0;
   const bool live_edges = feats || (D.flags & F_LIVE_EDGES);
-  if (live_edges) {
-    sum_out = ld_relaxed64(&rs->sum_out);
-    local_edges = ld_relaxed64(&C->local_edges);
-  }
+  // with G^T and a complete AC-4 work list the live-edge count follows from
+  // running totals (the scheduler flavours keep it without F_LIVE_EDGES)
+  const bool by_counts = D.ioff != nullptr && (D.flags & F_AC4_POSSIBLE) &&
+                         ((MODES & M_SCHED) || live_edges);
+  if (live_edges) sum_out = ld_relaxed64(&rs->sum_out);
+  if (by_counts) local_edges = ld_relaxed64(&C->local_edges);
   if (feats) {
     sum_in = ld_relaxed64(&rs->sum_in);
     h0 = ld_relaxed(&rs->hist[0]);
@@ -926,13 +964,10 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
   // only removed successors, so every edge that touches one ends in one).
   // Otherwise: with G^T, the same from the in-degree sums; without it, out-edges
   // of live vertices (AC-3/AC-6 know each removed vertex's degree).
-  if (live_edges) {
-    // (in-edges pushed from local queues belong to removed vertices without
-    // work-list entries)
-    if (D.ioff != nullptr && (D.flags & F_AC4_POSSIBLE))
-      L.m_live = (unsigned long long)D.m - e_end - local_edges;
-    else L.m_live -= (D.ioff != nullptr) ? sum_in : sum_out;
-  }
+  // (in-edges pushed from local queues belong to removed vertices without
+  // work-list entries)
+  if (by_counts) L.m_live = (unsigned long long)D.m - e_end - local_edges;
+  else if (live_edges) L.m_live -= (D.ioff != nullptr) ? sum_in : sum_out;
   if (nF == 0) {
     L.done = 1;
   } else {
@@ -955,30 +990,55 @@ __device__ ROUND_FN void advance(const Dev& D, Cta& B) {
       f[11] = (r >= 1) ? (float)L.variant : -1.0f;  // the variant whose state is current
     }
     uint32_t next;
-    if (!(MODES & M_SCHED) || D.mode <= TRIM_AC3_PULL) {
-      next = D.mode;
-    } else if (D.mode == TRIM_SCHED_SCRIPTED) {
+    bool confident = false;  // the learned scheduler may commit at once
+    if (!(MODES & M_SCHED) || B.mode <= TRIM_AC3_PULL) {
+      next = B.mode;
+    } else if (!consult) {
+      next = L.variant;  // inside a committed stretch
+    } else if (B.mode == TRIM_SCHED_SCRIPTED) {
       next = D.script_len ? D.script[r % D.script_len] : 0u;
       if (next > 2u) next = TRIM_AC3_PULL;
       if (next == TRIM_AC4_PUSH && D.ioff == nullptr) next = TRIM_AC3_PULL;
     } else {
       next = heuristic_choice(D, L, nF, n_live, w_end, e_end);
-      if (D.mode == TRIM_SCHED_LEARNED && D.model != nullptr) {
+      if (B.mode == TRIM_SCHED_LEARNED && D.model != nullptr) {
         bool in_range = false;
+        float conf = 0.0f;
 #if TRIM_MODES & 8
-        const uint32_t learned = mlp_choice(D, B.model, f, &in_range);
+        const uint32_t learned = mlp_choice(D, f, &in_range, &conf);
 #else
         const uint32_t learned = next;
 #endif
-        if (in_range) next = learned;
+        if (in_range) {
+          next = learned;
+          confident = D.commit_confidence > 0.0f && conf >= D.commit_confidence;
+        }
       }
     }
-    // rounds in a row with an unchanged choice. A flavour without the
-    // schedulers makes no choice: it runs a committed stretch, and leaves the
-    // count one short of a commit, so that when the stretch ends one round in
-    // which the resumed scheduler confirms the variant re-commits the run.
-    L.stable = !(MODES & M_SCHED) ? (D.commit_after ? D.commit_after - 1u : 0u)
-               : (r >= 1 && next == L.variant) ? L.stable + 1u : 1u;
+    // rounds in a row with an unchanged choice. After commit_after of them
+    // (or a learned choice at or above commit_confidence) the run commits: the
+    // next recheck_rounds rounds (doubling while the same commit repeats) run
+    // the variant without consulting the scheduler or gathering features, and
+    // the count stays one short of a commit, so that the first consulted round
+    // after the stretch re-commits if the scheduler keeps the variant.
+    if (!consult) {
+      L.stable = D.commit_after ? D.commit_after - 1u : 0u;
+    } else {
+      L.stable = (r >= 1 && next == L.variant) ? L.stable + 1u : 1u;
+      if (confident) L.stable = max(L.stable, D.commit_after);
+      L.cstop = 0u;
+      if (D.commit_after != 0u && L.stable >= D.commit_after) {
+        const uint32_t p0 = D.recheck_rounds ? D.recheck_rounds : 1u;
+        const uint32_t p = (next == L.clast && L.cperiod) ? min(L.cperiod * 2u, 1u << 30) : p0;
+        L.cperiod = p;
+        L.clast = next;
+        const unsigned long long stop = (unsigned long long)r + 1u + p;
+        L.cstop = stop > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)stop;
+        L.stable = D.commit_after - 1u;
+        if (cta0 && r == 0u) C->commit_round0 = 1u;
+      }
+      if (cta0) C->consults += 1u;
+    }
     L.prev_variant = (r >= 1) ? L.variant : NIL;
     L.fprev = L.fe - L.fb;  // frontier of round r, for the timing feature two rounds on
     L.variant = next;
@@ -1097,14 +1157,41 @@ __device__ ROUND_FN void ac4_round(const Dev& D, Cta& B, const Sched& S, uint32_
 #if TRIM_LOCAL
 // ------------------------------------------------------------------ local AC-4 rounds
 
+// End of a local stretch that returns to ordinary rounds (all threads): the
+// queued vertices of round r (buffer b) become work-list entries, and the round
+// ends like an ordinary one (flush, grid barrier, advance). A rare path, out of
+// line in the scheduler flavour so that its flush and scheduler code add no
+// registers to the local rounds.
+#if TRIM_MODES & 8
+__device__ __noinline__
+#else
+__device__ __forceinline__
+#endif
+void local_leave(const Dev& D, Cta& B, uint32_t b, uint32_t r) {
+  const unsigned lane = lane_id();
+  const uint32_t ne = B.lq_vend[b];
+  for (uint32_t i0 = (threadIdx.x >> 5) * 32u; i0 < ne; i0 += blockDim.x) {
+    const uint32_t i = i0 + lane;
+    const bool has = i < ne;
+    append_w4(D, B, has, has ? B.lq_row[b][i] : 0u, has ? B.lq_din[b][i] : 0u, r);
+  }
+  flush_round(D, B, r, D.live0);
+  if ((D.flags & F_ROUND_LOG) && blockIdx.x == 0 && threadIdx.x == 0)
+    D.C->t_flush[r & 3] = globaltimer();
+  if (!grid_barrier(D, B, false)) return;
+  if (threadIdx.x < 32) advance(D, B);
+  __syncthreads();
+}
+
 // Does round S.round start a stretch of local rounds? Its pending work-list
 // entries (the stretch's first round gives each warp whole entries) must have
 // at most local_edges_max in-edges in all, none more than 256.
-__device__ __forceinline__ bool local_start(const Dev& D, const Sched& S, uint32_t nwarps) {
+__device__ __forceinline__ bool local_start(const Dev& D, const Sched& S) {
   if (D.local_edges_max == 0u || S.variant != TRIM_AC4_PUSH) return false;
-  if (D.stop_round != 0u && S.round + 1u >= D.stop_round) return false;
+  // with the schedulers: inside a committed stretch only, whose last round
+  // (the one the scheduler reads features of) runs as an ordinary round
+  if ((MODES & M_SCHED) && !(S.cstop != 0u && S.round + 1u < S.cstop)) return false;
   const uint32_t edges = S.e_end - S.e_c4;
-  (void)nwarps;
   return edges <= D.local_edges_max && S.bmax <= 256u;
 }
 
@@ -1135,10 +1222,12 @@ __device__ void local_close(const Dev& D, Cta& B, uint32_t nF) {
       rec->t_end_ns = globaltimer();
       rec->t_work_ns = C->t_work[r & 3];
       rec->t_flush_ns = rec->t_work_ns;  // a local round moves nothing to global lists
-      for (int i = 0; i < NFEAT; ++i) rec->features[i] = 0.0f;
+      for (int i = 0; i < NFEAT; ++i) rec->features[i] = L.feat[i];  // that chose round r
       C->rlog_len = r;
     }
   }
+  // round r+1 is chosen without the scheduler (a committed or fixed variant)
+  for (int i = 0; i < NFEAT; ++i) L.feat[i] = 0.0f;
   if (nF == 0u) {
     L.done = 1u;
     return;
@@ -1165,7 +1254,7 @@ __device__ bool local_barrier(const Dev& D, Cta& B, uint32_t b, uint32_t r) {
   if (threadIdx.x == 0) {
     Sched& S = B.S;
     const uint32_t slot = S.lround & 1u;
-    if ((D.flags & F_LIVE_EDGES) && B.lq_pushed)
+    if (((MODES & M_SCHED) || (D.flags & F_LIVE_EDGES)) && B.lq_pushed)
       atomicAdd(&D.C->local_edges, (unsigned long long)B.lq_pushed);
     const unsigned long long add =
         (1ull << 48) | ((unsigned long long)B.lq_ovf << 32) | (unsigned long long)B.lq_k;
@@ -1192,7 +1281,7 @@ __device__ bool local_barrier(const Dev& D, Cta& B, uint32_t b, uint32_t r) {
     S.lbase[slot] = cur;
     S.lround += 1u;
     const uint32_t nF = (uint32_t)d, n_ovf = (uint32_t)(d >> 32) & 0xFFFFu;
-    const bool stop = D.stop_round != 0u && r + 1u >= D.stop_round;
+    const bool stop = (MODES & M_SCHED) && r + 1u >= S.cstop;
     if (n_ovf == 0u && (nF == 0u || !stop)) {
       local_close(D, B, nF);  // every removal of the round is in the queues
       B.lq_next = nF ? LQ_GO : LQ_DONE;
@@ -1217,7 +1306,8 @@ __device__ bool local_barrier(const Dev& D, Cta& B, uint32_t b, uint32_t r) {
 // queue; every decrement loads the G^T row bounds of its vertex alongside the
 // atomic, so a removal costs no further dependent load before its row is
 // queued. The stretch ends when a round removes nothing (the run is done),
-// when a round overflowed the queues, or at the host's stop round; in the last
+// when a round overflowed the queues, or (with the schedulers) before the last
+// round of the committed stretch; in the last
 // two cases the queued vertices join the global work list and the round ends
 // like an ordinary one (flush, grid barrier, advance). Returns false on a
 // timeout.
@@ -1289,20 +1379,7 @@ __device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
       first = false;
       continue;
     }
-    // back to ordinary rounds: this round's queued vertices become work-list
-    // entries, and the round ends like an ordinary one
-    const uint32_t ne = B.lq_vend[b];
-    for (uint32_t i0 = (threadIdx.x >> 5) * 32u; i0 < ne; i0 += blockDim.x) {
-      const uint32_t i = i0 + lane;
-      const bool has = i < ne;
-      append_w4(D, B, has, has ? B.lq_row[b][i] : 0u, has ? B.lq_din[b][i] : 0u, r);
-    }
-    flush_round(D, B, r, D.live0);
-    if ((D.flags & F_ROUND_LOG) && blockIdx.x == 0 && threadIdx.x == 0)
-      D.C->t_flush[r & 3] = globaltimer();
-    if (!grid_barrier(D, B, false)) break;
-    if (threadIdx.x < 32) advance(D, B);
-    __syncthreads();
+    local_leave(D, B, b, r);
     break;
   }
   stats_flush(D, B, K);
@@ -1757,9 +1834,27 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t nwarps = gridDim.x * wpb;
   const uint32_t gwarp = blockIdx.x * wpb + (threadIdx.x >> 5);
+  if (D.flags & F_CONTINUE) {
+    // enqueued behind a run's first segment: resume the run if that segment
+    // handed it over; else (the run is over or failed) return at once
+    if (threadIdx.x == 0) {
+      const volatile Ctrl* C = D.C;
+      B.skip = (C->err == 0u && C->resume != 0u) ? 0u : 1u;
+    }
+    __syncthreads();
+    if (B.skip) return;  // every CTA read the same control block: all return
+  }
   if (threadIdx.x == 0) {
     Sched& S = B.S;
-    B.bar_base = D.bar_base;
+    if (D.flags & F_CONTINUE) {
+      B.resume = 1u;
+      B.bar_base = ((const volatile Ctrl*)D.C)->bar;
+    } else {
+      B.resume = D.resume;
+      B.bar_base = D.bar_base;
+    }
+    B.mode = D.mode;
+    if (blockIdx.x == 0) D.C->segments += 1u;
     S.round = 0; S.fb = 0; S.fe = 0;
     S.variant = NIL; S.prev_variant = NIL;
     S.c4w = 0; S.e_c4 = 0; S.w_end = 0; S.e_end = 0;
@@ -1767,6 +1862,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     S.done = 0; S.fprev = 0; S.mixed = 0;
     S.vcount[0] = S.vcount[1] = S.vcount[2] = 0;
     S.stable = 0;
+    S.cstop = 0; S.cperiod = 0; S.clast = NIL;
     S.bmax = 0;
     S.m_live = D.m;
     for (int i = 0; i < NFEAT; ++i) S.feat[i] = 0.0f;
@@ -1792,18 +1888,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     B.lq_k = B.lq_ovf = B.lq_pushed = 0;
 #endif
   }
-#if TRIM_MODES & 8
-  // blob layout W1[32][12] b1 W2[32][32] b2 W3[3][32] b3 mean istd lo hi; W1 and
-  // W2 are stored transposed in shared memory
-  if (D.model != nullptr)
-    for (int i = threadIdx.x; i < TRIM_MLP_NBLOB; i += blockDim.x) {
-      int dst = i;
-      if (i < 384) dst = (i % 12) * 32 + i / 12;
-      else if (i >= 416 && i < 1440) dst = 416 + ((i - 416) % 32) * 32 + (i - 416) / 32;
-      B.model[dst] = __ldg(&D.model[i]);
-    }
-#endif
-  if (D.resume && threadIdx.x == 0) {
+  if (threadIdx.x == 0 && B.resume) {
     // continue a run that an earlier segment left at the start of round saved.round
     const volatile uint32_t* w = reinterpret_cast<const volatile uint32_t*>(&D.C->saved);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&B.S);
@@ -1811,7 +1896,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
   }
   __syncthreads();
   bool ok = true;
-  if (!D.resume) {
+  if (!B.resume) {
     start_round(D, 0);
     if (threadIdx.x == 0) B.w4_wide = (MODES & M_INOUT) ? 0u : 1u;
     __syncthreads();
@@ -1826,7 +1911,7 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     // advance() publishes this before any work-list append
     if (threadIdx.x == 0) B.w4_wide = 0;
   }
-  bool fresh = !D.resume;  // a resumed segment starts with its round already chosen
+  bool fresh = !B.resume;  // a resumed segment starts with its round already chosen
   while (ok) {
     if (fresh && threadIdx.x < 32) advance(D, B);  // also reads the error flag
     fresh = true;
@@ -1840,26 +1925,24 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
     const bool have = (S.variant == TRIM_AC4_PUSH && (MODES & M_AC4)) ||
                       (S.variant == TRIM_AC6_SUPPORT && (MODES & M_AC6)) ||
                       (S.variant == TRIM_AC3_PULL && (MODES & M_AC3));
-    // Hand the run to the host at the start of this round (every CTA takes the
-    // same decision from the same state, so all stop here): this kernel lacks
-    // the chosen variant; or the host asked to get the run back at this round;
-    // or the scheduler kept its choice long enough to commit to it.
-    const bool stop = D.stop_round != 0u && S.round >= D.stop_round;
-    const bool commit = (MODES & M_SCHED) && D.commit_after != 0u && S.stable >= D.commit_after;
-    if (!have || stop || commit) {
+    // This kernel lacks the variant chosen for this round: it saves the
+    // schedule state and hands the run over at the start of the round (every
+    // CTA takes the decision from the same state, so all stop here); the
+    // kernel that has the variant resumes it.
+    if (!have) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         volatile uint32_t* w = reinterpret_cast<volatile uint32_t*>(&D.C->saved);
         const uint32_t* src = reinterpret_cast<const uint32_t*>(&B.S);
         for (unsigned i = 0; i < sizeof(Sched) / 4; ++i) w[i] = src[i];
         D.C->resume_variant = S.variant;
-        D.C->commit = (have && !stop && commit) ? 1u : 0u;
+        if (D.C->first_exit_round == 0u) D.C->first_exit_round = S.round;
         __threadfence();
         D.C->resume = 1;
       }
       break;
     }
 #if TRIM_LOCAL
-    if (local_start(D, S, nwarps)) {
+    if (local_start(D, S)) {
       if (!local_stretch(D, B)) break;
       fresh = false;  // done, or the stretch's last round already ran advance()
       continue;

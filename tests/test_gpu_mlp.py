@@ -103,6 +103,7 @@ def test_in_kernel_choice_matches_reference_argmax():
         with P.Trimmer(g.off, g.tgt, flags=P.TRIM_FLAG_ROUND_LOG) as t:
             t.run("ac4")  # builds G^T so that all three variants are available
             t.set_model(blob.astype(np.float32))
+            t.set_params(sched_commit_rounds=0)  # the model decides every round
             t.run("learned")
             for rec in t.round_log():
                 f = np.array(rec.features, np.float32)
@@ -140,3 +141,60 @@ def test_trained_model_gains_over_the_heuristic():
             assert np.array_equal(t.level(device=False), lvl), mode
         assert runs[-1]["rounds_by_variant"] == [0, 0, alpha]
         assert times["learned"] < 0.9 * times["heuristic"], times
+
+
+def _median_run_ms(t, mode, flush, reps):
+    """Median time of `reps` complete asynchronous runs: CUDA events on the
+    library stream around trim_run_async (control-block reset and every kernel
+    of the run), the L2 flushed before each."""
+    import statistics
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(reps):
+        with torch.cuda.stream(t.stream):
+            flush.add_(1)
+        e0.record(t.stream)
+        t.run_async(mode)
+        e1.record(t.stream)
+        t.sync()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+@pytest.mark.parametrize("i", [1, 2])
+def test_learned_keeps_pace_with_the_best_fixed_variant(i):
+    """On the full-size rmat22 (4 rounds) and deep-cascade (2,868 rounds)
+    workloads with G^T, where AC-4 wins every round, the learned schedule (the
+    committed model, library defaults) must cost at most 5% more than the best
+    fixed variant: median of 9 timed runs each after warm-up, the schedules
+    interleaved in groups of 3. Results stay exact."""
+    import torch
+    import paper_2107_12720_gb300 as P
+    from paper_2107_12720_gb300 import scheduler as S
+    import oracle
+    g = cfg.config(i)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    oi, ti = oracle.transpose(g.off, g.tgt)
+    dev = lambda a: torch.from_numpy(a.astype(np.int32)).cuda()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    fixed = ["ac4", "ac6", "ac3"] if i == 1 else ["ac4", "ac6"]  # AC-3 takes 0.7 s on the cascade
+    with P.Trimmer(dev(g.off), dev(g.tgt), dev(oi), dev(ti), stream=stream) as t:
+        t.set_model(S.load_blob())
+        modes = fixed + ["learned"]
+        for mode in modes:
+            t.run(mode)
+            t.run(mode)
+        times = {m: [] for m in modes}
+        for _ in range(3):
+            for mode in modes:
+                times[mode].append(_median_run_ms(t, mode, flush, 3))
+        med = {m: float(np.median(v)) for m, v in times.items()}
+        s = t.run("learned")
+        assert np.array_equal(t.level(device=False), lvl)
+        assert s["rounds_by_variant"] == [alpha, 0, 0], s
+    best = min(med[m] for m in fixed)
+    assert best >= 0.95 * med["learned"], med

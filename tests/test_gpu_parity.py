@@ -188,17 +188,65 @@ def test_random_schedules_are_bit_identical():
 
 
 def _script_segments(sched, alpha):
-    """Kernel launches of a segmented scripted run: one, plus one per change of
+    """Segments of a host-segmented scripted run: one, plus one per change of
     variant between consecutive rounds (round k runs sched[(k-1) % len])."""
     v = [int(sched[(k - 1) % len(sched)]) for k in range(1, alpha + 1)]
     return 1 + sum(1 for a, b in zip(v, v[1:]) if a != b), v
 
 
+HANDOVERS = ("device", "host")
+
+
+def _handover(P, name):
+    return {"device": P.TRIM_HANDOVER_DEVICE, "host": P.TRIM_HANDOVER_HOST,
+            "none": P.TRIM_HANDOVER_NONE}[name]
+
+
+def _check_segments(s, handover, changes):
+    """Kernels of a scheduled run whose variant changes `changes` times between
+    rounds the first kernel cannot run: host-side handover, one segment per
+    change (reset + one launch each); device-side, the first kernel and, if it
+    handed over, the all-variant continuation (reset + 2 launches always)."""
+    if handover == "device":
+        assert s["segments"] == (1 if changes == 0 else 2), (s, changes)
+        assert s["launches"] == 3, s
+    elif handover == "host":
+        assert s["segments"] == 1 + changes, (s, changes)
+        assert s["launches"] == 1 + s["segments"], s
+    else:
+        assert s["segments"] == 1 and s["launches"] == 2, s
+
+
+def _consulted_rounds(alpha, K, P0):
+    """Rounds whose variant the scheduler chose when its choice never changes:
+    rounds 1..K; the choice for round K is the K-th in a row and commits the
+    run for the next P0 rounds, after which the scheduler reads the features
+    of round K+P0 and chooses round K+P0+1, re-committing for 2*P0 rounds, and
+    so on (doubling)."""
+    out = list(range(1, min(K, alpha) + 1))
+    r, p = K, P0
+    while True:
+        r += p + 1
+        if r > alpha:
+            return out
+        out.append(r)
+        p *= 2
+
+
+def _consults_in_log(t):
+    """Rounds of the round log whose variant the scheduler chose (a committed
+    round records no features)."""
+    return [r.round for r in t.round_log() if any(x != 0.0 for x in r.features)]
+
+
 def test_segmented_runs_match_single_launch():
-    """A scheduled trim_run runs as segments on the single-variant kernels; the
-    single all-variant launch of trim_run_async computes the same run. Both must
-    equal the oracle, run the scripted variant in every round, and the segmented
-    run must take exactly one launch per change of variant."""
+    """A scheduled run hands the run to another kernel when its scheduler picks
+    a variant the running kernel lacks: on the device (the all-variant kernel
+    enqueued behind the first one finishes the run) or by the host (one launch
+    per change); the single all-variant launch (TRIM_HANDOVER_NONE) computes the
+    same run. All must equal the oracle and run the scripted variant in every
+    round, with the launches each handover implies; trim_run_async of a
+    scheduled mode is the device-side run."""
     P = _P()
     rng = np.random.default_rng(17)
     for i in [1, 2, 4]:
@@ -212,43 +260,98 @@ def test_segmented_runs_match_single_launch():
             for sched in scheds:
                 t.set_schedule(sched)
                 want_segments, want_v = _script_segments(sched, alpha)
-                s = t.run("scripted")
-                check(t, lvl, st, alpha, f"segmented{sched}", s)
-                assert s["segments"] == want_segments, (i, sched, s["segments"], want_segments)
-                assert [r.variant for r in t.round_log()] == want_v
-                t.run_async("scripted")
-                s1 = t.sync()
-                check(t, lvl, st, alpha, f"single{sched}", s1)
-                assert s1["segments"] == 1
-                assert [r.variant for r in t.round_log()] == want_v
+                for h in HANDOVERS + ("none",):
+                    t.set_params(sched_handover=_handover(P, h))
+                    for run in ("sync", "async"):
+                        s = t.run("scripted") if run == "sync" else \
+                            (t.run_async("scripted"), t.sync())[1]
+                        check(t, lvl, st, alpha, f"{h}-{run}{sched}", s)
+                        assert [r.variant for r in t.round_log()] == want_v
+                        if run == "async" and h != "device":
+                            _check_segments(s, "none", 0)  # one all-variant launch
+                        else:
+                            _check_segments(s, h, want_segments - 1)
+                t.set_params(sched_handover=P.TRIM_HANDOVER_DEVICE)
             for mode in ["heuristic", "learned"]:
-                # without commits the segmented run takes the single launch's choices
-                t.set_params(sched_commit_rounds=0)
+                # without commits every segmented run takes the single launch's choices
+                t.set_params(sched_commit_rounds=0, sched_handover=P.TRIM_HANDOVER_NONE)
                 s = t.run(mode)
-                check(t, lvl, st, alpha, mode, s)
-                seg_v = [r.variant for r in t.round_log()]
-                changes = sum(1 for a, b in zip(seg_v, seg_v[1:]) if a != b)
-                assert s["segments"] in (1 + changes, 2 + changes)
-                t.run_async(mode)
-                check(t, lvl, st, alpha, mode + "-single", t.sync())
-                assert [r.variant for r in t.round_log()] == seg_v
+                check(t, lvl, st, alpha, mode + "-single", s)
+                one_v = [r.variant for r in t.round_log()]
+                for h in HANDOVERS:
+                    t.set_params(sched_handover=_handover(P, h))
+                    s = t.run(mode)
+                    check(t, lvl, st, alpha, f"{mode}-{h}", s)
+                    assert [r.variant for r in t.round_log()] == one_v, (mode, h)
                 # with commits: same result, rounds split over the kernels as logged
-                t.set_params(sched_commit_rounds=4, sched_recheck_rounds=16)
-                s = t.run(mode)
-                check(t, lvl, st, alpha, mode + "-commit", s)
-                log = t.round_log()
-                assert len(log) == alpha
-                assert list(np.bincount([r.variant for r in log], minlength=3)) == \
-                    list(s["rounds_by_variant"])
-                t.set_params(sched_commit_rounds=32, sched_recheck_rounds=128)
+                for h in HANDOVERS + ("none",):
+                    t.set_params(sched_commit_rounds=4, sched_recheck_rounds=16,
+                                 sched_handover=_handover(P, h))
+                    s = t.run(mode)
+                    check(t, lvl, st, alpha, f"{mode}-commit-{h}", s)
+                    log = t.round_log()
+                    assert len(log) == alpha
+                    assert list(np.bincount([r.variant for r in log], minlength=3)) == \
+                        list(s["rounds_by_variant"])
+                t.set_params(sched_commit_rounds=8, sched_recheck_rounds=128,
+                             sched_handover=P.TRIM_HANDOVER_DEVICE)
+
+
+def _confident_ac4_model():
+    """A hand-set scheduler MLP (the TRIM_MLP_NBLOB layout) whose logits are
+    (10, 0, -10) for every input: AC-4 with softmax probability 0.99995."""
+    import paper_2107_12720_gb300 as P
+    nin, nh = P.abi.TRIM_MLP_NIN, P.abi.TRIM_MLP_NH
+    zeros = lambda *shape: np.zeros(shape, np.float32)
+    norm = [zeros(nin), np.ones(nin, np.float32), np.full(nin, -1e30, np.float32),
+            np.full(nin, 1e30, np.float32)]
+    blob = np.concatenate([zeros(nh, nin).ravel(), zeros(nh), zeros(nh, nh).ravel(), zeros(nh),
+                           zeros(3, nh).ravel(), np.array([10.0, 0.0, -10.0], np.float32),
+                           *norm])
+    assert blob.size == P.abi.TRIM_MLP_NBLOB
+    return blob
+
+
+@pytest.mark.parametrize("i", [1, 2])
+def test_confident_choice_commits_at_once(i):
+    """A learned choice at or above sched_commit_confidence commits the run at
+    once: the scheduler chooses round 1, then only the rounds after each
+    committed stretch (16, 32, 64, ... rounds), all within the first kernel
+    (one segment); with confidence 0 it commits after sched_commit_rounds
+    unchanged choices instead. The consulted rounds are read from the round log
+    (a committed round records no features); every run equals the oracle."""
+    P = _P()
+    g = cfg.config_small(i)
+    lvl, st, alpha = oracle.peel(g.off, g.tgt)
+    off, tgt = dev_csr(g)
+    oi, ti = dev_csr_in(g)
+    P0 = 16
+    with P.Trimmer(off, tgt, oi, ti, flags=P.TRIM_FLAG_ROUND_LOG) as t:
+        t.set_model(_confident_ac4_model())
+        for h in HANDOVERS + ("none",):
+            for conf, K in ((0.9, 1), (0.0, 8)):
+                t.set_params(sched_recheck_rounds=P0, sched_handover=_handover(P, h),
+                             sched_commit_confidence=conf)
+                s = t.run("learned")
+                check(t, lvl, st, alpha, f"learned-{h}-{conf}", s)
+                assert s["rounds_by_variant"] == [alpha, 0, 0]
+                _check_segments(s, h, 0)
+                assert _consults_in_log(t) == _consulted_rounds(alpha, K, P0), (h, conf)
+                if K == 1 and alpha <= P0 and h != "none":
+                    # the run ended inside round 1's stretch: the next one is
+                    # that schedule on the AC-4-only kernel, without the scheduler
+                    s = t.run("learned")
+                    check(t, lvl, st, alpha, f"learned-{h}-known", s)
+                    assert s["rounds_by_variant"] == [alpha, 0, 0]
+                    assert s["launches"] == 2 and _consults_in_log(t) == [], s
 
 
 def test_committed_stretches_on_a_deep_cascade():
     """A deep cascade (hundreds of rounds) with the heuristic choosing AC-4 every
-    round: after sched_commit_rounds stable rounds the run moves to the AC-4-only
-    kernel for stretches of 16, 32, 64, ... rounds, consulting the scheduler
-    between them. The launch count follows from that rule exactly; the levels
-    equal the oracle's."""
+    round: after sched_commit_rounds unchanged choices the run commits for
+    stretches of 16, 32, 64, ... rounds and consults the scheduler only between
+    them, inside one kernel. The consulted rounds follow that rule exactly; the
+    levels equal the oracle's."""
     P = _P()
     g = cfg.config_small(2)
     lvl, st, alpha = oracle.peel(g.off, g.tgt)
@@ -256,11 +359,14 @@ def test_committed_stretches_on_a_deep_cascade():
     oi, ti = dev_csr_in(g)
     K, P0 = 4, 16
     with P.Trimmer(off, tgt, oi, ti, flags=P.TRIM_FLAG_ROUND_LOG) as t:
-        t.set_params(sched_commit_rounds=K, sched_recheck_rounds=P0)
-        s = t.run("heuristic")
-        check(t, lvl, st, alpha, "heuristic-commit", s)
-        assert s["rounds_by_variant"] == [alpha, 0, 0]
-        assert s["segments"] == _commit_segments(alpha, K, P0), (s["segments"], alpha)
+        for h in HANDOVERS + ("none",):
+            t.set_params(sched_commit_rounds=K, sched_recheck_rounds=P0,
+                         sched_handover=_handover(P, h))
+            s = t.run("heuristic")
+            check(t, lvl, st, alpha, f"heuristic-commit-{h}", s)
+            assert s["rounds_by_variant"] == [alpha, 0, 0]
+            _check_segments(s, h, 0)
+            assert _consults_in_log(t) == _consulted_rounds(alpha, K, P0), h
 
 
 def _first_round_ac6_model():
@@ -327,11 +433,12 @@ def test_local_rounds_match_ordinary_rounds():
                 check(t, lvl, st, alpha, f"local{edges}-{g.name}", t.run("ac4"))
 
 
-def test_committed_stretches_leave_local_rounds_at_the_stop_round():
+def test_committed_stretches_end_local_rounds_before_the_scheduler_reads():
     """A scheduled run without a round log: its committed AC-4 stretches run
-    local rounds and must hand the run back to the scheduler exactly at the
-    stop round (queued vertices join the global work list), so the launch
-    count follows the commit rule and the levels equal the oracle's."""
+    local rounds in the scheduler kernel, which must end before the last round
+    of each stretch (that round is an ordinary one, whose features the
+    scheduler reads); the levels equal the oracle's, every in-edge of a removed
+    vertex is pushed exactly once, and local rounds did run."""
     P = _P()
     for i, K, P0 in [(2, 4, 16), (2, 3, 5), (4, 2, 7), (0, 1, 3)]:
         g = cfg.config_small(i)
@@ -339,34 +446,18 @@ def test_committed_stretches_leave_local_rounds_at_the_stop_round():
         off, tgt = dev_csr(g)
         oi, ti = dev_csr_in(g)
         with P.Trimmer(off, tgt, oi, ti, flags=P.TRIM_FLAG_STATS) as t:
-            t.set_params(sched_commit_rounds=K, sched_recheck_rounds=P0)
-            s = t.run("heuristic")
-            check(t, lvl, st, alpha, f"heuristic-commit[{i}]", s)
-            assert s["rounds_by_variant"] == [alpha, 0, 0]
-            assert s["segments"] == _commit_segments(alpha, K, P0), (i, s["segments"], alpha)
             din = np.diff(oracle.transpose(g.off, g.tgt)[0].astype(np.int64))
-            assert s["in_edges_pushed"] == int(din[st == 0].sum())
-
-
-def _commit_segments(alpha, K, P0):
-    """Launches of a scheduled run whose choice never changes: rounds 1..alpha;
-    the choice has been kept for K rounds at the start of round K, where the run
-    commits; a stretch from round r runs to the start of round r+p (p = P0,
-    doubling); the scheduler then runs round r+p and, keeping its choice,
-    re-commits at the start of round r+p+1."""
-    segs, r, p = 1, K, P0
-    if r > alpha:
-        return segs
-    while True:
-        segs += 1                # committed stretch from round r
-        end = r + p
-        if end > alpha:          # the run ends inside the stretch
-            return segs
-        segs += 1                # scheduler kernel for round `end`
-        r = end + 1
-        if r > alpha:
-            return segs
-        p *= 2
+            for h in HANDOVERS:
+                t.set_params(sched_commit_rounds=K, sched_recheck_rounds=P0,
+                             sched_handover=_handover(P, h))
+                for mode in ("heuristic", "learned"):
+                    s = t.run(mode)
+                    check(t, lvl, st, alpha, f"{mode}-commit[{i}]-{h}", s)
+                    assert s["rounds_by_variant"] == [alpha, 0, 0]
+                    _check_segments(s, h, 0)
+                    assert s["in_edges_pushed"] == int(din[st == 0].sum())
+                    if i == 2:
+                        assert s["local_rounds"] > 0, s
 
 
 def test_targets_at_any_alignment():
