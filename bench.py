@@ -589,6 +589,32 @@ def implicit_comparison(P, flush, stream, steps=3):
     return out
 
 
+def gt_build_ms(P, bufs, flush, stream, reps=3):
+    """Device-side G^T build on a context given only the out-CSR (device
+    arrays): CUDA events on the library stream around the first AC-4 run, which
+    builds G^T before its launch, minus the same run on the built G^T; median
+    over `reps` fresh contexts."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(t):
+        flush.add_(1)
+        e0.record(stream)
+        t.run_async("ac4")
+        e1.record(stream)
+        t.sync()
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    out = []
+    for _ in range(reps):
+        with P.Trimmer(bufs[0], bufs[1], stream=stream) as t:
+            first = timed(t)
+            out.append(first - statistics.median(timed(t) for _ in range(3)))
+    return statistics.median(out)
+
+
 def extra_workload(P, idx, args, flush, stream, model):
     """A second workload timed in the same run (all its schedules; for the
     batched workload also each graph trimmed alone), as a sub-object of the
@@ -611,11 +637,15 @@ def extra_workload(P, idx, args, flush, stream, model):
         if idx == 1:
             sampling = vertex_sampling(P, t, g, flush)
         scc = scc_timing(t, g)
+    gt_ms = gt_build_ms(P, bufs, flush, stream) if not batched else None
     out = {"workload": wname, "n": g.n, "m": g.m, "variants": sweep,
            "schedules": schedules_summary(sweep)}
     if sampling:
         out["vertex_sampling"] = sampling
     out["scc"] = scc
+    if gt_ms is not None:
+        out["gt_build_ms"] = gt_ms
+        print(f"# [{idx}] device G^T build {gt_ms:.3f} ms", file=sys.stderr, flush=True)
     if batched:
         out["graphs"] = int(len(g.graph_off) - 1)
         out["timing"] = ("CUDA events around trim_batch_run: one replayed CUDA graph "

@@ -349,6 +349,16 @@ trim_err_t trim_level(const trim_ctx* ctx, uint32_t* out, int out_on_device);
  * run or trim_destroy): lets callers read results without a copy. */
 trim_err_t trim_level_device_ptr(const trim_ctx* ctx, const uint32_t** out);
 
+/* The context's transposed graph G^T (Section 2's in-edges, as CSR): in_offsets
+ * n+1 values, in_targets m values, the predecessors of v in
+ * in_targets[in_offsets[v] .. in_offsets[v+1]) (their order within a row is
+ * unspecified). If the context was created without csr_in, G^T is built on
+ * the device first (and kept for AC-4 runs). Both outputs on the device if
+ * out_on_device, else on the host. Fails with TRIM_ERR_INVALID_ARG on an
+ * implicit graph. */
+trim_err_t trim_in_csr(trim_ctx* ctx, uint32_t* in_offsets, uint32_t* in_targets,
+                       int out_on_device);
+
 /* Batched trimming of G independent graphs packed into the context's CSR:
  * graph g owns vertices [graph_off[g], graph_off[g+1]) and no edge may cross two
  * graphs (checked with TRIM_FLAG_VALIDATE). graph_off: G+1 host uint32 values,

@@ -26,7 +26,7 @@ from .abi import (LIB_PATH, TRIM_MASKED, TRIM_AC3_PULL, TRIM_AC4_PUSH, TRIM_AC6_
 from .abi import (trim_batch_run, trim_create, trim_create_implicit, trim_default_params,
                   trim_destroy,
                   trim_get_params, trim_get_round_log, trim_last_error, trim_level,
-                  trim_level_device_ptr, trim_mlp_adam_step, trim_mlp_forward, trim_mlp_loss_grad,
+                  trim_level_device_ptr, trim_in_csr, trim_mlp_adam_step, trim_mlp_forward, trim_mlp_loss_grad,
                   trim_mlp_scratch_bytes, trim_run, trim_run_async, trim_run_inout, trim_run_scc,
                   trim_set_alloc_limit, trim_set_dead_mask,
                   trim_set_model, trim_set_params, trim_set_schedule, trim_status, trim_sync)
@@ -179,6 +179,14 @@ class Trimmer:
         out = np.empty(self.n, np.uint32)
         trim_level(self.ctx, out.ctypes.data, 0)
         return out
+
+    def in_csr(self):
+        """G^T as host arrays (in_offsets, in_targets); built on the device
+        first if the context was created without it (see trim_in_csr)."""
+        off = np.empty(self.n + 1, np.uint32)
+        tgt = np.empty(max(int(self.m), 1), np.uint32)
+        trim_in_csr(self.ctx, off.ctypes.data, tgt.ctypes.data, 0)
+        return off, tgt[:int(self.m)]
 
     def status(self, device: bool = True):
         import torch

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("trim_status", _I, [_P, _P, _I]),
     ("trim_level", _I, [_P, _P, _I]),
     ("trim_level_device_ptr", _I, [_P, ctypes.POINTER(_P)]),
+    ("trim_in_csr", _I, [_P, _P, _P, _I]),
     ("trim_batch_run", _I, [_P, _P, _U32, _I, ctypes.POINTER(TrimRunStats)]),
     ("trim_set_params", _I, [_P, ctypes.POINTER(TrimParams)]),
     ("trim_get_params", _I, [_P, ctypes.POINTER(TrimParams)]),
@@ -199,6 +200,10 @@ def trim_status(ctx, out_ptr, on_device: int) -> None:
 
 def trim_level(ctx, out_ptr, on_device: int) -> None:
     check(lib().trim_level(ctx, _ptr(out_ptr), on_device), ctx)
+
+
+def trim_in_csr(ctx, off_ptr, tgt_ptr, on_device: int) -> None:
+    check(lib().trim_in_csr(ctx, _ptr(off_ptr), _ptr(tgt_ptr), on_device), ctx)
 
 
 def trim_level_device_ptr(ctx) -> int:

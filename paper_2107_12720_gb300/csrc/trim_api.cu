@@ -165,6 +165,17 @@ trim_err_t dalloc(trim_ctx* c, T** p, size_t count) {
   return TRIM_OK;
 }
 
+// Returns a temporary allocation of dalloc to the pool (stream-ordered).
+template <class T>
+void dfree(trim_ctx* c, T* p, size_t count) {
+  if (!p) return;
+  auto it = std::find(c->owned.begin(), c->owned.end(), static_cast<void*>(p));
+  if (it == c->owned.end()) return;
+  c->owned.erase(it);
+  c->allocated -= std::max<size_t>(count, 1) * sizeof(T);
+  cudaFreeAsync(p, c->stream);
+}
+
 // Carves 256-byte aligned pieces out of one device allocation (an "arena"),
 // so a context costs one cudaMalloc and one cudaFree instead of one per array.
 struct ArenaPlan {
@@ -353,31 +364,84 @@ trim_err_t device_scan(trim_ctx* c, const uint32_t* in, uint32_t n, uint32_t* ou
   return TRIM_OK;
 }
 
-// G^T by counting sort on the device (the transposed graph of Section 2).
+// G^T on the device (the transposed graph of Section 2), by a counting sort
+// whose counts and placements are shared-memory atomics (trim_gt_*_kernel: no
+// same-address global atomics on hub targets); graphs with more than 2^27
+// vertices use the direct global counting sort.
 trim_err_t build_transpose(trim_ctx* c) {
-  uint32_t *ioff = nullptr, *itgt = nullptr, *fill = nullptr, *bad = nullptr;
-  TRY(dalloc(c, &ioff, (size_t)c->n + 1));
-  TRY(dalloc(c, &itgt, c->m));
-  TRY(dalloc(c, &fill, (size_t)c->n + 1));
-  TRY(dalloc(c, &bad, 1));
-  CK(cudaMemsetAsync(fill, 0, ((size_t)c->n + 1) * 4, c->stream));
-  CK(cudaMemsetAsync(bad, 0, 4, c->stream));
-  const int blocks = c->sm_count * 8;
-  if (c->m) {
-    trim_indeg_kernel<<<blocks, 512, 0, c->stream>>>(c->tgt, c->m, c->n, fill, bad);
+  const uint32_t n = c->n;
+  const uint32_t m = (uint32_t)c->m;  // offsets are uint32: m < 2^32
+  uint32_t *ioff = nullptr, *itgt = nullptr;
+  TRY(dalloc(c, &ioff, (size_t)n + 1));
+  TRY(dalloc(c, &itgt, m));
+  uint32_t lg = 0;
+  while (lg < 32 && (1ull << lg) < n) ++lg;
+  if (m == 0) {
+    CK(cudaMemsetAsync(ioff, 0, ((size_t)n + 1) * 4, c->stream));
+  } else if (lg <= 27) {
+    // buckets of 2^shift targets, at most 32,768 each (128 KB of counters in
+    // pass 4): up to 2^26 vertices 2,048 buckets and two CTAs per SM in passes
+    // 1 and 3 (96 KB of shared memory each in pass 3), above that 4,096
+    // buckets and one CTA per SM; either way the open sectors of all (bucket,
+    // CTA) ranges, 32 B each, stay in the L2
+    const bool wide = lg > 26;
+    const uint32_t keep = wide ? 12u : 11u;
+    const uint32_t shift = lg > keep ? lg - keep : 0;
+    const uint32_t nb = (uint32_t)(((uint64_t)n + (1u << shift) - 1) >> shift);
+    const uint32_t C = (uint32_t)c->sm_count * (wide ? 1u : 2u);
+    const uint32_t rows = (n + C - 1) / C;
+    // (bucket, CTA) ranges hold whole sectors: up to 3 unused slots each
+    const size_t cap = (size_t)m + 3 * (size_t)nb * C;
+    uint32_t *counts = nullptr, *slots = nullptr, *real = nullptr, *rstart = nullptr;
+    unsigned long long* pairs = nullptr;
+    TRY(dalloc(c, &counts, (size_t)nb * C));
+    TRY(dalloc(c, &slots, (size_t)nb * C + 1));
+    TRY(dalloc(c, &real, nb));
+    TRY(dalloc(c, &rstart, (size_t)nb + 1));
+    TRY(dalloc(c, &pairs, cap));
+    CK(cudaMemsetAsync(real, 0, (size_t)nb * 4, c->stream));
+    const size_t hist_bytes = (size_t)nb * 4, scatter_bytes = (size_t)nb * 48;
+    const size_t place_bytes = ((size_t)1 << shift) * 4;
+    CK(cudaFuncSetAttribute(trim_gt_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)scatter_bytes));
+    CK(cudaFuncSetAttribute(trim_gt_place_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)place_bytes));
+    trim_gt_hist_kernel<<<C, 1024, hist_bytes, c->stream>>>(c->off, c->tgt, n, rows, shift, nb,
+                                                            counts, real);
     CK(cudaGetLastError());
-  }
-  TRY(device_scan(c, fill, c->n, ioff));
-  CK(cudaMemsetAsync(fill, 0, ((size_t)c->n + 1) * 4, c->stream));
-  if (c->m) {
-    trim_transpose_fill_kernel<<<blocks, 512, 0, c->stream>>>(c->off, c->tgt, c->n, ioff, fill,
-                                                             itgt);
+    TRY(device_scan(c, counts, nb * C, slots));
+    TRY(device_scan(c, real, nb, rstart));
+    trim_gt_scatter_kernel<<<C, 1024, scatter_bytes, c->stream>>>(c->off, c->tgt, n, rows, shift,
+                                                                  nb, slots, pairs);
     CK(cudaGetLastError());
+    trim_gt_place_kernel<<<std::min<uint32_t>(nb, (uint32_t)c->sm_count * 4), 512, place_bytes,
+                           c->stream>>>(pairs, slots, rstart, C, n, m, shift, nb, ioff, itgt);
+    CK(cudaGetLastError());
+    dfree(c, pairs, cap);
+    dfree(c, rstart, (size_t)nb + 1);
+    dfree(c, real, nb);
+    dfree(c, slots, (size_t)nb * C + 1);
+    dfree(c, counts, (size_t)nb * C);
+  } else {
+    uint32_t *fill = nullptr, *bad = nullptr;
+    TRY(dalloc(c, &fill, (size_t)n + 1));
+    TRY(dalloc(c, &bad, 1));
+    CK(cudaMemsetAsync(fill, 0, ((size_t)n + 1) * 4, c->stream));
+    CK(cudaMemsetAsync(bad, 0, 4, c->stream));
+    const int blocks = c->sm_count * 8;
+    trim_indeg_kernel<<<blocks, 512, 0, c->stream>>>(c->tgt, m, n, fill, bad);
+    CK(cudaGetLastError());
+    TRY(device_scan(c, fill, n, ioff));
+    CK(cudaMemsetAsync(fill, 0, ((size_t)n + 1) * 4, c->stream));
+    trim_transpose_fill_kernel<<<blocks, 512, 0, c->stream>>>(c->off, c->tgt, n, ioff, fill, itgt);
+    CK(cudaGetLastError());
+    dfree(c, bad, 1);
+    dfree(c, fill, (size_t)n + 1);
   }
   TRY(sync_check(c));
   c->ioff = ioff;
-  forget_first_flavours(c);
   c->itgt = itgt;
+  forget_first_flavours(c);
   return TRIM_OK;
 }
 
@@ -1310,6 +1374,19 @@ trim_err_t trim_level(const trim_ctx* cc, uint32_t* out, int out_on_device) {
   CK(cudaMemcpyAsync(out, c->level, (size_t)c->n * 4,
                      out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      c->stream));
+  return sync_check(c);
+}
+
+trim_err_t trim_in_csr(trim_ctx* c, uint32_t* in_offsets, uint32_t* in_targets,
+                       int out_on_device) {
+  if (!c || !in_offsets || (!in_targets && c->m))
+    return fail(c, TRIM_ERR_INVALID_ARG, "null argument");
+  if (c->implicit) return fail(c, TRIM_ERR_INVALID_ARG, "an implicit graph has no CSR");
+  if (c->pending) TRY(finish_run(c, nullptr));
+  if (c->ioff == nullptr) TRY(build_transpose(c));
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(in_offsets, c->ioff, ((size_t)c->n + 1) * 4, kind, c->stream));
+  if (c->m) CK(cudaMemcpyAsync(in_targets, c->itgt, (size_t)c->m * 4, kind, c->stream));
   return sync_check(c);
 }
 

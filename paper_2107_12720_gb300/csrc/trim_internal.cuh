@@ -221,6 +221,19 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned x) {
   }
   return x;
 }
+
+// Warp-collective search: owner lane j of element k, i.e. the largest j with
+// excl_j <= k (lanes that own nothing carry excl = total and are never picked).
+__device__ __forceinline__ unsigned owner_of(unsigned excl, unsigned k) {
+  unsigned lo = 0;
+#pragma unroll
+  for (unsigned step = 16; step >= 1; step >>= 1) {
+    const unsigned cand = lo + step;
+    const unsigned ex = __shfl_sync(0xFFFFFFFFu, excl, cand & 31u);
+    if (cand < 32u && ex <= k) lo = cand;
+  }
+  return lo;
+}
 template <class T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll
@@ -284,6 +297,16 @@ __global__ void trim_scan_blocks_kernel(const uint32_t* in, uint32_t n, uint32_t
                                         uint32_t* block_sums, uint32_t chunk);
 __global__ void trim_scan_apply_kernel(uint32_t* out, uint32_t n, const uint32_t* block_sums,
                                        uint32_t nblocks, uint32_t chunk);
+__global__ void trim_gt_hist_kernel(const uint32_t* off, const uint32_t* tgt, uint32_t n,
+                                    uint32_t rows, uint32_t shift, uint32_t nb, uint32_t* counts,
+                                    uint32_t* real);
+__global__ void trim_gt_scatter_kernel(const uint32_t* off, const uint32_t* tgt, uint32_t n,
+                                       uint32_t rows, uint32_t shift, uint32_t nb,
+                                       const uint32_t* slots, unsigned long long* pairs);
+__global__ void trim_gt_place_kernel(const unsigned long long* pairs, const uint32_t* slots,
+                                     const uint32_t* rstart, uint32_t C, uint32_t n, uint32_t m,
+                                     uint32_t shift, uint32_t nb, uint32_t* ioff,
+                                     uint32_t* itgt);
 __global__ void trim_transpose_fill_kernel(const uint32_t* off, const uint32_t* tgt, uint32_t n,
                                            const uint32_t* ioff, uint32_t* fill, uint32_t* itgt);
 __global__ void trim_validate_offsets_kernel(const uint32_t* off, uint32_t n, uint64_t m,

@@ -171,19 +171,6 @@ __device__ __forceinline__ void red_relaxed_add(unsigned* p, unsigned v) {
   asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Warp-collective search: owner lane j of element k, i.e. the largest j with
-// excl_j <= k (lanes that own nothing carry excl = total and are never picked).
-__device__ __forceinline__ unsigned owner_of(unsigned excl, unsigned k) {
-  unsigned lo = 0;
-#pragma unroll
-  for (unsigned step = 16; step >= 1; step >>= 1) {
-    const unsigned cand = lo + step;
-    const unsigned ex = __shfl_sync(FULL, excl, cand & 31u);
-    if (cand < 32u && ex <= k) lo = cand;
-  }
-  return lo;
-}
-
 // ------------------------------------------------------------------ rows
 
 #if TRIM_MODES & 32
