@@ -129,6 +129,7 @@ struct Cta {
   unsigned mode;      // trim_variant_t of the run
   unsigned err;
   unsigned w4_wide;   // initial pass: the work-list slices take all four buffers
+  unsigned lq_scratch;  // initial pass with a dead mask: deferred heavy rows
   unsigned long long kstat[4];  // TRIM_FLAG_STATS totals of this CTA (see stats_flush)
   uint32_t wbuf[MAX_WARPS][WBUF];
 #if TRIM_LOCAL
@@ -1750,63 +1751,150 @@ __device__ ROUND_FN void init_round(const Dev& D, Cta& B, uint32_t gwarp, uint32
 // is DEAD from the start: level 0 (removed before round 1 for every variant),
 // counter 0 (a decrement can never return 1), never on the work list, not
 // counted. An unmasked vertex counts its unmasked successors: with none it is
-// removed in round 0, else it is LIVE with that count as its AC-4 counter. A
-// run without AC-4 needs no count, only whether one unmasked successor exists,
-// so its scans stop at the first one. One lane per vertex; rows longer than 32
-// are scanned by the whole warp.
+// removed in round 0, else it is LIVE with that count as its AC-4 counter.
+// With AC-4 every edge of an unmasked vertex is counted: each warp takes 32
+// vertices and walks their edges laid end to end, 32 per step with four
+// steps' loads in flight; a vertex's count in a step is the popcount of the
+// step's unmasked-target ballot over the lanes that hold its edges. Rows with
+// more than kMaskHeavy edges are left to the whole CTA afterwards (one warp
+// would walk a skewed graph's longest row alone). A run
+// without AC-4 needs only whether one unmasked successor exists, so each lane
+// scans its own row and stops at the first one (rows longer than 32: the
+// whole warp).
+__device__ __forceinline__ uint32_t lane_range(uint32_t a, uint32_t b) {  // bits [a, b), b <= 32
+  const uint32_t hi = b >= 32u ? 0xFFFFFFFFu : ((1u << b) - 1u);
+  const uint32_t lo = a >= 32u ? 0xFFFFFFFFu : ((1u << a) - 1u);
+  return hi & ~lo;
+}
+
+constexpr uint32_t kMaskHeavy = 1024;
+constexpr uint32_t kMaskHeavyCap = LW - MAX_WARPS;  // list + per-warp sums in one slice
+
 __device__ ROUND_FN void init_round_masked(const Dev& D, Cta& B, uint32_t gwarp,
                                            uint32_t nwarps) {
   const unsigned lane = lane_id();
   const uint32_t n = D.n;
   const bool w4 = (D.flags & F_AC4_POSSIBLE) != 0;
-  const bool rows = D.ioff != nullptr;
+  // the CTA's deferred heavy rows and its reduction scratch: warp 0's live-list
+  // slice, which no append of this pass uses (its work-list slices stay in
+  // buffers 1 and 2: w4_wide is 0 here)
+  uint32_t* heavy = slice(0, 3);
+  uint32_t* wsum = heavy + kMaskHeavyCap;
+  if (threadIdx.x == 0) B.lq_scratch = 0u;
+  __syncthreads();
   for (uint32_t base = gwarp * 32u; base < n; base += nwarps * 32u) {
     const uint32_t v = base + lane;
     const bool has = v < n;
     const bool masked = has && D.mask[v] != 0;
     const uint32_t s = has ? __ldg(&D.off[v]) : 0u;
     const uint32_t d = has ? __ldg(&D.off[v + 1]) - s : 0u;
-    const uint32_t i0 = (has && rows) ? __ldg(&D.ioff[v]) : 0u;
-    const uint32_t i1 = (has && rows) ? __ldg(&D.ioff[v + 1]) : 0u;
-    const bool own = has && !masked && d <= 32u;  // counted by its own lane
     uint32_t c = 0;
-    for (uint32_t k0 = 0; k0 < (own ? d : 0u) && (w4 || c == 0u); k0 += 4u) {
-      uint32_t t[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) t[q] = (k0 + q < d) ? __ldg(&D.tgt[s + k0 + q]) : 0u;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) c += (k0 + q < d && D.mask[t[q]] == 0) ? 1u : 0u;
+    bool deferred = false;
+    if (w4 && !masked && d > kMaskHeavy) {
+      const uint32_t at = atomicAdd(&B.lq_scratch, 1u);
+      if (at < kMaskHeavyCap) {
+        heavy[at] = v;
+        deferred = true;
+      }
     }
-    unsigned big = __ballot_sync(FULL, has && !masked && d > 32u);
-    while (big) {
-      const int j = __ffs(big) - 1;
-      big &= big - 1u;
-      const uint32_t sj = __shfl_sync(FULL, s, j), dj = __shfl_sync(FULL, d, j);
-      uint32_t part = 0;
-      // 128 entries per step, four loads in flight per lane; only a run
-      // without AC-4 stops early (the vote would serialise the AC-4 count)
-      for (uint32_t k0 = 0; k0 < dj; k0 += 128u) {  // warp-uniform
+    if (w4) {
+      const uint32_t dd = (masked || deferred) ? 0u : d;
+      const uint32_t incl = warp_incl_scan(dd), excl = incl - dd;
+      const uint32_t total = __shfl_sync(FULL, incl, 31);
+      for (uint32_t k0 = 0; k0 < total; k0 += 128u) {  // warp-uniform
         uint32_t t[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t k = k0 + (uint32_t)q * 32u + lane;
-          t[q] = k < dj ? __ldg(&D.tgt[sj + k]) : 0u;
+          const unsigned o = owner_of(excl, k);
+          const uint32_t so = __shfl_sync(FULL, s, o), xo = __shfl_sync(FULL, excl, o);
+          t[q] = k < total ? __ldg(&D.tgt[so + (k - xo)]) : 0u;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const uint32_t k = k0 + (uint32_t)q * 32u + lane;
-          part += (k < dj && D.mask[t[q]] == 0) ? 1u : 0u;
+          const uint32_t cs = k0 + (uint32_t)q * 32u;  // flattened index of lane 0
+          const bool live = cs + lane < total && D.mask[t[q]] == 0;
+          const uint32_t bal = __ballot_sync(FULL, live);
+          const uint32_t a = excl <= cs ? 0u : min(excl - cs, 32u);
+          const uint32_t e = excl + dd;
+          const uint32_t b = e <= cs ? 0u : min(e - cs, 32u);
+          c += __popc(bal & lane_range(a, b));
         }
-        if (!w4 && __any_sync(FULL, part != 0u)) break;
       }
-      part = __reduce_add_sync(FULL, part);
-      if ((int)lane == j) c = part;
+    } else {
+      const bool own = has && !masked && d <= 32u;  // scanned by its own lane
+      for (uint32_t k0 = 0; k0 < (own ? d : 0u) && c == 0u; k0 += 4u) {
+        uint32_t tq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tq[q] = (k0 + q < d) ? __ldg(&D.tgt[s + k0 + q]) : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c += (k0 + q < d && D.mask[tq[q]] == 0) ? 1u : 0u;
+      }
+      unsigned big = __ballot_sync(FULL, has && !masked && d > 32u);
+      while (big) {
+        const int j = __ffs(big) - 1;
+        big &= big - 1u;
+        const uint32_t sj = __shfl_sync(FULL, s, j), dj = __shfl_sync(FULL, d, j);
+        uint32_t part = 0;
+        for (uint32_t k0 = 0; k0 < dj; k0 += 128u) {  // warp-uniform
+          uint32_t tq[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t k = k0 + (uint32_t)q * 32u + lane;
+            tq[q] = k < dj ? __ldg(&D.tgt[sj + k]) : 0u;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t k = k0 + (uint32_t)q * 32u + lane;
+            part += (k < dj && D.mask[tq[q]] == 0) ? 1u : 0u;
+          }
+          if (__any_sync(FULL, part != 0u)) break;
+        }
+        part = __reduce_add_sync(FULL, part);
+        if ((int)lane == j) c = part;
+      }
     }
-    if (has) {
+    // (a deferred row is counted below; every lane takes part in append_dead,
+    // a warp-collective call)
+    if (has && !deferred) {
       D.level[v] = (masked || c == 0u) ? 0u : LIVE;
       if (w4) D.cnt[v] = masked ? 0u : c;
     }
-    append_dead(D, B, has && !masked && c == 0u, v, 0u, D.live0, true, true, i0, i1 - i0);
+    append_dead(D, B, has && !masked && !deferred && c == 0u, v, 0u, D.live0, true);
+  }
+  __syncthreads();
+  const uint32_t nh = min(B.lq_scratch, kMaskHeavyCap);
+  const unsigned warp = threadIdx.x >> 5;
+  for (uint32_t h = 0; h < nh; ++h) {  // block-uniform
+    const uint32_t v = heavy[h];
+    const uint32_t s = __ldg(&D.off[v]), e = __ldg(&D.off[v + 1]);
+    uint32_t part = 0;
+    for (uint32_t k0 = s; k0 < e; k0 += 4u * blockDim.x) {
+      uint32_t tq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t k = k0 + (uint32_t)q * blockDim.x + threadIdx.x;
+        tq[q] = k < e ? __ldg(&D.tgt[k]) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t k = k0 + (uint32_t)q * blockDim.x + threadIdx.x;
+        part += (k < e && D.mask[tq[q]] == 0) ? 1u : 0u;
+      }
+    }
+    part = __reduce_add_sync(FULL, part);
+    if (lane == 0) wsum[warp] = part;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t c = lane < (blockDim.x >> 5) ? wsum[lane] : 0u;
+      c = __reduce_add_sync(FULL, c);
+      if (lane == 0) {
+        D.level[v] = c ? LIVE : 0u;
+        D.cnt[v] = c;
+      }
+      append_dead(D, B, lane == 0 && c == 0u, v, 0u, D.live0, true);
+    }
+    __syncthreads();
   }
 }
 #endif
@@ -1885,7 +1973,8 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
   bool ok = true;
   if (!B.resume) {
     start_round(D, 0);
-    if (threadIdx.x == 0) B.w4_wide = (MODES & M_INOUT) ? 0u : 1u;
+    // (the initial pass with a dead mask keeps buffer 3 for its heavy rows)
+    if (threadIdx.x == 0) B.w4_wide = ((MODES & M_INOUT) || D.mask != nullptr) ? 0u : 1u;
     __syncthreads();
 #if !(TRIM_MODES & 48)
     if (D.mask != nullptr) init_round_masked(D, B, gwarp, nwarps);
