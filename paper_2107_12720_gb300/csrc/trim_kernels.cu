@@ -1214,8 +1214,10 @@ __device__ void local_close(const Dev& D, Cta& B, uint32_t nF) {
       C->rlog_len = r;
     }
   }
-  // round r+1 is chosen without the scheduler (a committed or fixed variant)
-  for (int i = 0; i < NFEAT; ++i) L.feat[i] = 0.0f;
+  // round r+1 is chosen without the scheduler (a committed or fixed variant;
+  // a flavour without the schedulers never sets features)
+  if (MODES & M_SCHED)
+    for (int i = 0; i < NFEAT; ++i) L.feat[i] = 0.0f;
   if (nF == 0u) {
     L.done = 1u;
     return;
