@@ -74,3 +74,17 @@ def test_edgeless_and_single():
 
 def test_full_rmat22():
     _check(cfg.config(1))
+
+
+def test_above_2_27_vertices():
+    """Graphs with more than 2^27 vertices take the direct global counting
+    sort (the two-level build's per-bucket counters would not fit a CTA):
+    134,217,731 vertices, 300,000 random edges, a third of them into one hub."""
+    g = _random((1 << 27) + 3, 300_000, seed=27, hubs=1, hub_share=0.33)
+    _check(g)
+
+
+def test_widest_buckets():
+    """2^26 + 1 vertices: the two-level build's widest buckets (32,768 targets,
+    128 KB of counters in the placement pass), 2,000,000 edges."""
+    _check(_random((1 << 26) + 1, 2_000_000, seed=26, hubs=5, hub_share=0.2))
