@@ -133,6 +133,14 @@ typedef struct {
                                  trim_batch_run) uses, and who passes the run between
                                  them when the scheduler picks a variant the running
                                  kernel lacks: TRIM_HANDOVER_*                           */
+  uint32_t async_round_edges; /* AC-4 (alone or as a committed scheduled variant), from
+                                 round 8 on: once the in-edges still to push are at most
+                                 this many, the rest of the run is asynchronous: no
+                                 rounds, each CTA pushes the rows of the vertices it
+                                 removes at its own pace, and a removed vertex takes one
+                                 more than the top level among its successors (Definition
+                                 2), carried by the pushes. Same levels and alpha; needs
+                                 G^T, off in TRIM_FLAG_ROUND_LOG runs (0 = never)        */
 } trim_params_t;
 
 /* trim_params_t.sched_handover */
@@ -163,6 +171,11 @@ typedef struct {
   uint32_t local_rounds;    /* AC-4 rounds that ran CTA-locally (see local_round_edges)   */
   uint32_t launches;        /* kernel launches of the run: the control-block reset, every
                                segment, a continuation launch, a dead-mask pass          */
+  uint32_t async_round;     /* round from which the run was asynchronous (0: never; see
+                               async_round_edges)                                        */
+  uint32_t async_removed;   /* vertices the asynchronous part removed                   */
+  uint32_t async_rebalances; /* times the asynchronous part spread its pending work evenly
+                               over the CTAs again                                       */
 } trim_run_stats_t;
 
 /* One record per round of a TRIM_FLAG_ROUND_LOG run. features[] are the
@@ -196,7 +209,9 @@ typedef struct trim_ctx trim_ctx;
  * when TRIM_FLAG_VALIDATE is set); without it the AC-4 variant builds G^T on the
  * device on first use (a counting sort; its time is not part of trim_run).
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
- * On success *out receives the context. Allocates device memory ~ (40 n + 4 m) B. */
+ * On success *out receives the context. Allocates device memory ~ (40 n + 4 m) B,
+ * plus ~ (20 n + m / 64) B + 128 B per resident GPU thread for the asynchronous
+ * AC-4 tail once G^T exists (given here, or built on first use). */
 trim_err_t trim_create(const trim_csr_t* csr_out, const trim_csr_t* csr_in, void* cuda_stream,
                        uint32_t flags, trim_ctx** out);
 

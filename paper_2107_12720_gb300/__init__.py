@@ -241,4 +241,6 @@ def _stats_dict(s: TrimRunStats) -> dict:
             "edges_inspected": s.edges_inspected, "in_edges_pushed": s.in_edges_pushed,
             "candidates": s.candidates, "live_swept": s.live_swept,
             "rounds_by_variant": list(s.rounds_by_variant), "segments": s.segments,
-            "local_rounds": s.local_rounds, "launches": s.launches}
+            "local_rounds": s.local_rounds, "launches": s.launches,
+            "async_round": s.async_round, "async_removed": s.async_removed,
+            "async_rebalances": s.async_rebalances}

@@ -44,7 +44,8 @@ class TrimParams(ctypes.Structure):
                 ("sched_commit_rounds", ctypes.c_uint32), ("sched_recheck_rounds", ctypes.c_uint32),
                 ("spin_limit_ns", ctypes.c_uint64), ("heur_push_ratio", ctypes.c_float),
                 ("heur_ac6_ratio", ctypes.c_float), ("local_round_edges", ctypes.c_uint32),
-                ("sched_commit_confidence", ctypes.c_float), ("sched_handover", ctypes.c_uint32)]
+                ("sched_commit_confidence", ctypes.c_float), ("sched_handover", ctypes.c_uint32),
+                ("async_round_edges", ctypes.c_uint32)]
 
 
 class TrimImplicitGraph(ctypes.Structure):
@@ -65,7 +66,8 @@ class TrimRunStats(ctypes.Structure):
                 ("in_edges_pushed", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("live_swept", ctypes.c_uint64), ("rounds_by_variant", ctypes.c_uint32 * 3),
                 ("segments", ctypes.c_uint32), ("local_rounds", ctypes.c_uint32),
-                ("launches", ctypes.c_uint32)]
+                ("launches", ctypes.c_uint32), ("async_round", ctypes.c_uint32),
+                ("async_removed", ctypes.c_uint32), ("async_rebalances", ctypes.c_uint32)]
 
 
 class TrimRoundRec(ctypes.Structure):

@@ -41,6 +41,13 @@ struct trim_ctx {
            *s_next = nullptr, *s_cnt = nullptr, *s_off = nullptr, *s_list = nullptr,
            *log = nullptr, *roff = nullptr, *live0 = nullptr, *live1 = nullptr, *bsum = nullptr;
   uint32_t *w4_row = nullptr, *w4_eoff = nullptr, *chunk_first = nullptr;
+  // asynchronous AC-4 tail: per-vertex words, the global list of G^T row
+  // pieces and the two rebalance entry lists (allocated once G^T exists)
+  unsigned long long* aw = nullptr;
+  uint32_t *oq_row = nullptr, *oq_len = nullptr, *oq_lev = nullptr;
+  uint32_t oq_cap = 0;
+  uint32_t *ae_id = nullptr, *ae_lev = nullptr;
+  uint32_t ae_cap = 0;
   // in+out runs: in-degree counters, the work list's G rows and in-degrees, and
   // the chunk-owner index of its edge space (both rows: up to 2m edges)
   uint32_t *cnt_in = nullptr, *w4_orow = nullptr, *w4_din = nullptr, *chunk_io = nullptr;
@@ -273,6 +280,7 @@ void default_params(trim_params_t* p) {
   p->local_round_edges = 1u << 18;
   p->sched_commit_confidence = 0.9f;
   p->sched_handover = TRIM_HANDOVER_DEVICE;
+  p->async_round_edges = 1u << 18;
 }
 
 // per-warp append slices in dynamic shared memory: 4 buffers (dead log, AC-4
@@ -364,6 +372,27 @@ trim_err_t device_scan(trim_ctx* c, const uint32_t* in, uint32_t n, uint32_t* ou
   return TRIM_OK;
 }
 
+// The asynchronous AC-4 tail's per-vertex words, its global list of G^T row
+// pieces and its two rebalance entry lists, allocated once G^T exists
+// (kernels without them never start the tail). An entry list holds every
+// queue of a cooperative grid: 8 entries per resident thread.
+trim_err_t alloc_async(trim_ctx* c) {
+  if (c->aw != nullptr) return TRIM_OK;
+  const uint64_t cap = trimk::async_queue_cap(c->n, c->m);  // < 2^32: n <= 2^31, m < 2^32
+  int per_sm = 0;
+  CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, c->device));
+  const uint64_t ecap = (uint64_t)c->sm_count * (uint64_t)per_sm * 8u;
+  TRY(dalloc(c, &c->aw, c->n));
+  TRY(dalloc(c, &c->oq_row, cap));
+  TRY(dalloc(c, &c->oq_len, cap));
+  TRY(dalloc(c, &c->oq_lev, cap));
+  TRY(dalloc(c, &c->ae_id, 2 * ecap));
+  TRY(dalloc(c, &c->ae_lev, 2 * ecap));
+  c->oq_cap = (uint32_t)cap;
+  c->ae_cap = (uint32_t)ecap;
+  return TRIM_OK;
+}
+
 // G^T on the device (the transposed graph of Section 2), by a counting sort
 // whose counts and placements are shared-memory atomics (trim_gt_*_kernel: no
 // same-address global atomics on hub targets); graphs with more than 2^27
@@ -441,6 +470,7 @@ trim_err_t build_transpose(trim_ctx* c) {
   TRY(sync_check(c));
   c->ioff = ioff;
   c->itgt = itgt;
+  TRY(alloc_async(c));
   forget_first_flavours(c);
   return TRIM_OK;
 }
@@ -616,6 +646,7 @@ trim_err_t create_impl(const trim_csr_t* g, const trim_csr_t* gi, void* stream, 
   c->w4_row = at(a_w4r); c->w4_eoff = at(a_w4e); c->chunk_first = at(a_chunk);
   if (c->rlog_cap) c->rlog = reinterpret_cast<trim_round_rec_t*>(base + a_rlog);
   if (flags & TRIM_FLAG_VALIDATE) TRY(validate(c, gi ? c->ioff : nullptr));
+  if (c->ioff != nullptr) TRY(alloc_async(c));
   CK(cudaMemsetAsync(c->s_cnt, 0, n * 4, c->stream));
   c->h_ctrl = take_ctrl_slot();
   c->h_ctrl_pinned = c->h_ctrl != nullptr;
@@ -803,6 +834,10 @@ trim_err_t enqueue_run(trim_ctx* c, trim_variant_t variant, int seg_flavour = -1
   D.commit_confidence = c->params.sched_commit_confidence;
   D.recheck_rounds = c->params.sched_recheck_rounds;
   D.local_edges_max = c->params.local_round_edges;
+  D.aw = c->aw;
+  D.oq_row = c->oq_row; D.oq_len = c->oq_len; D.oq_lev = c->oq_lev; D.oq_cap = c->oq_cap;
+  D.ae_id = c->ae_id; D.ae_lev = c->ae_lev; D.ae_cap = c->ae_cap;
+  D.async_edges_max = (c->aw != nullptr && c->ioff != nullptr) ? c->params.async_round_edges : 0u;
   // scheduled runs keep the live-edge count (a feature); with G^T and AC-4 the
   // scheduler kernels derive it from running totals instead
   if (variant >= TRIM_SCHED_HEURISTIC && !(ac4 && c->ioff)) D.flags |= trimk::F_LIVE_EDGES;
@@ -1156,6 +1191,9 @@ trim_err_t finish_run(trim_ctx* c, trim_run_stats_t* stats, bool ctrl_read) {
     s.segments = (uint32_t)c->last_segments;
     s.local_rounds = h.local_rounds;
     s.launches = (uint32_t)std::min<uint64_t>(launches, 0xFFFFFFFFu);
+    s.async_round = h.a_round;
+    s.async_removed = h.a_removed;
+    s.async_rebalances = h.a_rebalances;
     c->last = s;
     c->ran = true;
   }

@@ -18,6 +18,14 @@ namespace trimk {
 constexpr uint32_t LIVE = 0xFFFFFFFFu;
 constexpr uint32_t NIL = 0xFFFFFFFFu;
 constexpr int NFEAT = 12;
+// asynchronous AC-4 tail: in-edges per item of the shared queue (a removed
+// vertex's G^T row is cut into pieces of at most this many), and the queue's
+// capacity for n vertices and m edges (every removal adds at most
+// ceil(in-degree / kAsyncPiece) items)
+constexpr uint32_t kAsyncPiece = 256;
+__host__ __device__ constexpr uint64_t async_queue_cap(uint64_t n, uint64_t m) {
+  return n + m / kAsyncPiece + 1;
+}
 
 // flags inside Dev::flags (superset of the public TRIM_FLAG_*)
 constexpr uint32_t F_STATS = TRIM_FLAG_STATS;
@@ -104,7 +112,22 @@ struct Ctrl {
   unsigned long long local_edges; // in-edges pushed from the CTAs' local queues (live-edge count)
   unsigned int n_dead;            // removals so far, published by CTA 0
   unsigned int local_rounds;      // local AC-4 rounds so far, published by CTA 0
-  unsigned int _p5[28];
+  // asynchronous AC-4 tail (see async_tail in trim_kernels.cu): work tokens
+  // (one per CTA with work; 0: the run is over), pieces written to the global
+  // list, the rebalance generation asked for, entries in the two global entry
+  // lists, the tail's removals and top level, the round at which it took
+  // over, a heartbeat of the CTAs with work (bounds the wait of those
+  // without), and the rebalances run
+  unsigned int a_tokens;
+  unsigned int oq_res;
+  unsigned int a_req;
+  unsigned int e_n[2];
+  unsigned int a_removed;
+  unsigned int a_maxlev;
+  unsigned int a_round;
+  unsigned int a_beat;
+  unsigned int a_rebalances;
+  unsigned int _p5[18];
   // segmented runs: a kernel that lacks the variant its scheduler picked saves
   // the schedule state here and exits; the kernel that has it resumes from it
   unsigned int resume;            // 1: a segment ended early, state in `saved`
@@ -159,6 +182,20 @@ struct Dev {
   uint32_t recheck_rounds;  // length of the first committed stretch (doubles while repeated)
   uint32_t bar_base;  // grid-barrier counter when this kernel starts (0 for a new run)
   uint32_t local_edges_max;  // AC-4: pending in-edges up to which rounds run locally (0: never)
+  // asynchronous AC-4 tail: per vertex (top level among its removed successors
+  // << 32 | live-successor counter); the global list of G^T row pieces still
+  // to push (row start, length, level of the removed vertex) and its
+  // capacity; the two global entry lists of rebalances (predecessor, level),
+  // ae_cap entries each
+  unsigned long long* aw;
+  uint32_t* oq_row;
+  uint32_t* oq_len;
+  uint32_t* oq_lev;
+  uint32_t oq_cap;
+  uint32_t* ae_id;
+  uint32_t* ae_lev;
+  uint32_t ae_cap;
+  uint32_t async_edges_max;  // pending in-edges up to which the rest of the run is asynchronous (0: never)
   Ctrl* C;
   trim_round_rec_t* rlog;
   uint32_t rlog_cap;

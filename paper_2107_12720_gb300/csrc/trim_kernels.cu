@@ -116,6 +116,9 @@ struct WarpSlice {
 constexpr uint32_t LQ_EDGES = 1024;   // predecessors queued per CTA per round
 constexpr uint32_t LQ_ENTRIES = 256;  // removed vertices queued per CTA per round
 constexpr uint32_t LQ_DMAX = 64;      // larger in-degrees always go to the global work list
+// asynchronous AC-4 tail (see async_tail)
+constexpr uint32_t ASYNC_MIN_ROUND = 8;  // rounds before the tail may take over
+constexpr uint32_t AQ_LOCAL_DMAX = 1024; // larger in-degrees always go to the shared queue
 #endif
 
 // Per-CTA shared state.
@@ -144,6 +147,25 @@ struct Cta {
   uint32_t lq_ovf;                    // 1: a removal of this round went to the global lists
   uint32_t lq_pushed;                 // predecessors decremented from the queue this round
   uint32_t lq_next;                   // how the stretch goes on after the local barrier
+  // asynchronous tail: predecessors queued per buffer (dynamic shared memory):
+  // reserved, and the end of the reservations that fit; the share of the last
+  // rebalance (global entries [sh_elo, sh_ehi), pieces [sh_plo, sh_phi)); this
+  // CTA's removals and top level since it last released its token; whether it
+  // holds a token; steps run; whether it asks for a rebalance; rebalances
+  // passed; start of the pieces written since the last one; average share
+  // (entries) at the last one; its entry-list slot; what the next step does
+  uint32_t aq_res[2];
+  uint32_t aq_end[2];
+  uint32_t sh_elo, sh_ehi, sh_plo, sh_phi;
+  uint32_t a_removed, a_maxlev;
+  uint32_t a_token;
+  uint32_t a_steps;
+  uint32_t a_want;
+  uint32_t a_gen;
+  uint32_t a_plo;
+  uint32_t a_avg;
+  uint32_t a_base;
+  uint32_t a_next;
 #endif
 };
 
@@ -1176,6 +1198,10 @@ void local_leave(const Dev& D, Cta& B, uint32_t b, uint32_t r) {
 // at most local_edges_max in-edges in all, none more than 256.
 __device__ __forceinline__ bool local_start(const Dev& D, const Sched& S) {
   if (D.local_edges_max == 0u || S.variant != TRIM_AC4_PUSH) return false;
+  // where the asynchronous tail may take over from round ASYNC_MIN_ROUND on,
+  // no stretch starts before it (a stretch runs until the run is over)
+  if (D.async_edges_max != 0u && !(D.flags & F_ROUND_LOG) && S.round < ASYNC_MIN_ROUND)
+    return false;
   // with the schedulers: inside a committed stretch only, whose last round
   // (the one the scheduler reads features of) runs as an ordinary round
   if ((MODES & M_SCHED) && !(S.cstop != 0u && S.round + 1u < S.cstop)) return false;
@@ -1374,6 +1400,494 @@ __device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
   }
   stats_flush(D, B, K);
   return B.err == 0u;
+}
+
+// ------------------------------------------------------- asynchronous AC-4 tail
+//
+// A vertex's level is one more than the top level among its successors
+// (Definition 2: round r removes the vertices whose successors were all
+// removed before round r, the last of them in round r - 1). The pushes can
+// carry that maximum, and then the rest of an AC-4 run needs no rounds at all.
+// Every vertex gets one 64-bit word, (top level pushed so far << 32 |
+// live-successor counter); the push from a removed vertex of level l replaces
+// it by (max(top, l) << 32 | counter - 1) in one compare-and-swap, and the
+// push that takes the counter to zero removes the vertex with level
+// max(top, l) + 1: every successor has pushed by then, so the maximum is over
+// all of them, whatever the order of the pushes. No CTA waits for another:
+// each runs steps of its own. A step pushes the predecessors queued in the
+// CTA's shared memory (the G^T rows of the vertices it removed in its previous
+// step, each with its vertex's level) and queues those of the vertices it
+// removes now.
+//
+// A removed vertex's row stays with the CTA whose push removed it, and that
+// CTA is one of its successors' CTAs: over many levels the work drifts onto
+// fewer and fewer CTAs. A CTA whose queue holds far more than its share, or
+// whose removals do not fit its queue (those rows go to a global list of
+// pieces of at most kAsyncPiece in-edges), asks for a rebalance: every CTA
+// joins at its next step boundary, writes its queued entries to a global list,
+// and after a grid barrier each takes an even slice of those entries and of
+// the pieces written since the last rebalance, then a second barrier closes
+// the rebalance (counts published, the lists' counters ready for the next).
+// The tail ends when no CTA has work: a token count holds one token per CTA
+// with work; a CTA releases its token when its queue runs empty, and a count
+// of zero (with no rebalance asked for) ends the run.
+//
+// It takes over at the start of an AC-4 round r (r >= ASYNC_MIN_ROUND) whose
+// pending work-list entries are exactly the vertices removed in round r - 1,
+// at most async_edges_max in-edges, and runs the rest of the run (with the
+// schedulers: only inside a committed stretch, as the scheduler is not
+// consulted again).
+__device__ __forceinline__ bool async_start(const Dev& D, const Sched& S) {
+  if (D.async_edges_max == 0u || S.variant != TRIM_AC4_PUSH || S.mixed) return false;
+  if ((D.flags & F_ROUND_LOG) || S.round < ASYNC_MIN_ROUND) return false;
+  if (S.prev_variant != TRIM_AC4_PUSH) return false;
+  if ((MODES & M_SCHED) && D.mode > TRIM_AC3_PULL && !(S.cstop != 0u && S.round < S.cstop))
+    return false;
+  return S.e_end - S.e_c4 <= D.async_edges_max && S.bmax <= 256u;
+}
+
+// Warp-collective: lanes with ovf set removed a vertex (G^T row start row,
+// in-degree din, level lev) whose row goes to the global list of pieces, cut
+// into pieces of at most kAsyncPiece in-edges; the CTA then asks for a
+// rebalance. The pieces are read only after the rebalance's grid barrier.
+__device__ __noinline__ void async_spill(const Dev& D, Cta& B, bool ovf, uint32_t row,
+                                         uint32_t din, uint32_t lev) {
+  const unsigned lane = lane_id();
+  const uint32_t np = ovf ? (din + kAsyncPiece - 1u) / kAsyncPiece : 0u;
+  const uint32_t incl = warp_incl_scan(np);
+  const uint32_t tot = __shfl_sync(FULL, incl, 31);
+  uint32_t s = 0;
+  if (lane == 0) {
+    s = atomicAdd(&D.C->oq_res, tot);
+    B.a_want = 1u;
+  }
+  s = __shfl_sync(FULL, s, 0);
+  // (cannot fail: every removal adds at most ceil(din / kAsyncPiece) pieces)
+  if ((uint64_t)s + tot > D.oq_cap) {
+    if (lane == 0) set_error(D, TRIM_ERR_STATE, 5);
+    return;
+  }
+  if (ovf) {
+    const uint32_t at = s + incl - np;
+    for (uint32_t i = 0; i < np; ++i) {
+      D.oq_row[at + i] = row + i * kAsyncPiece;
+      D.oq_len[at + i] = min(kAsyncPiece, din - i * kAsyncPiece);
+      D.oq_lev[at + i] = lev;
+    }
+  }
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Warp-collective: lanes with `removed` set removed vertex p with level lev
+// (G^T row start row, in-degree din). The level is written and the
+// predecessors are queued in buffer nxt with that level, all of the warp's
+// rows at once (each lane loads entries of the flattened rows), each
+// predecessor's word and row bounds prefetched into L2 for the step that
+// pushes it; a row longer than AQ_LOCAL_DMAX, or one that does not fit, goes
+// to the global pieces.
+__device__ __forceinline__ void async_append(const Dev& D, Cta& B, bool removed, uint32_t p,
+                                             uint32_t lev, uint32_t row, uint32_t din,
+                                             uint32_t nxt, uint32_t QA) {
+  const unsigned lane = lane_id();
+  const unsigned mask = __ballot_sync(FULL, removed);
+  if (mask == 0u) return;
+  if (removed) D.level[p] = lev;
+  const uint32_t top = __reduce_max_sync(FULL, removed ? lev : 0u);
+  if (lane == 0) {
+    atomicAdd(&B.a_removed, (unsigned)__popc(mask));
+    atomicMax(&B.a_maxlev, top);
+  }
+  const bool want = removed && din > 0u && din <= AQ_LOCAL_DMAX;
+  bool ovf = removed && din > AQ_LOCAL_DMAX;
+  const unsigned wm = __ballot_sync(FULL, want);
+  if (wm) {
+    const unsigned ew = want ? din : 0u;
+    const unsigned eincl = warp_incl_scan(ew);
+    const unsigned esum = __shfl_sync(FULL, eincl, 31);
+    const unsigned excl = eincl - ew;
+    uint32_t be = 0;
+    if (lane == 0) be = atomicAdd(&B.aq_res[nxt], esum);
+    be = __shfl_sync(FULL, be, 0);
+    if ((uint64_t)be + esum <= QA) {  // warp-uniform
+      if (lane == 0) atomicMax(&B.aq_end[nxt], be + esum);
+      uint32_t* ids = dyn_smem + nxt * QA;
+      uint32_t* lv = dyn_smem + (2u + nxt) * QA;
+      for (uint32_t j0 = 0; j0 < esum; j0 += 128u) {
+        uint32_t t[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t j = j0 + (uint32_t)q * 32u + lane;
+          const unsigned o = owner_of(excl, j);
+          const uint32_t ro = __shfl_sync(FULL, row, o), xo = __shfl_sync(FULL, excl, o);
+          l[q] = __shfl_sync(FULL, lev, o);
+          t[q] = j < esum ? __ldg(&D.itgt[ro + (j - xo)]) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t j = j0 + (uint32_t)q * 32u + lane;
+          if (j < esum) {
+            ids[be + j] = t[q];
+            lv[be + j] = l[q];
+            prefetch_l2(&D.aw[t[q]]);  // for the step that pushes it
+            prefetch_l2(&D.ioff[t[q]]);
+          }
+        }
+      }
+    } else {
+      ovf = ovf || want;
+    }
+  }
+  if (__ballot_sync(FULL, ovf)) async_spill(D, B, ovf, row, din, lev);
+}
+
+// Warp-collective: pushes from removed vertices to their predecessors p[q]
+// (lanes with valid[q] set), each carrying its removed vertex's level l[q],
+// by compare-and-swap on the predecessors' words; the row bounds of every
+// predecessor load alongside its word, so a removal costs no further
+// dependent load before its row is queued. A word whose counter is zero
+// belongs to a vertex that is not live (masked): it is left alone.
+template <int Q>
+__device__ __forceinline__ void async_push(const Dev& D, Cta& B, const bool (&valid)[Q],
+                                           const uint32_t (&p)[Q], const uint32_t (&l)[Q],
+                                           uint32_t nxt, uint32_t QA, Counters& K) {
+  unsigned long long w[Q];
+  uint32_t p0[Q], p1[Q], lev[Q];
+  bool pend[Q], removed[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    w[q] = valid[q] ? ld_relaxed64(&D.aw[p[q]]) : 0ull;
+    p0[q] = valid[q] ? __ldg(&D.ioff[p[q]]) : 0u;
+    p1[q] = valid[q] ? __ldg(&D.ioff[p[q] + 1u]) : 0u;
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    pend[q] = valid[q] && (uint32_t)w[q] != 0u;
+    removed[q] = false;
+    lev[q] = 0u;
+    K.pushed += valid[q] ? 1u : 0u;
+  }
+  // a failed compare-and-swap means another push on the same word succeeded,
+  // so the loop ends; the bound only guards against a broken invariant
+  for (uint32_t it = 0;; ++it) {
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) any = any || pend[q];
+    if (!__any_sync(FULL, any)) break;
+    if (it == (1u << 22)) {
+      if (lane_id() == 0) set_error(D, TRIM_ERR_TIMEOUT, 6);
+      break;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      if (!pend[q]) continue;
+      const uint32_t top = max((uint32_t)(w[q] >> 32), l[q]);
+      const uint32_t cnt = (uint32_t)w[q];
+      const unsigned long long nw = ((unsigned long long)top << 32) | (cnt - 1u);
+      const unsigned long long prev = atomicCAS(&D.aw[p[q]], w[q], nw);
+      if (prev == w[q]) {
+        pend[q] = false;
+        removed[q] = cnt == 1u;
+        lev[q] = top + 1u;
+      } else {
+        w[q] = prev;
+        if ((uint32_t)prev == 0u) pend[q] = false;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    async_append(D, B, removed[q], p[q], lev[q], p0[q], p1[q] - p0[q], nxt, QA);
+}
+
+// Warp-collective: pushes the in-edges [row, row + len) of G^T, all carrying level l.
+__device__ __forceinline__ void async_piece(const Dev& D, Cta& B, uint32_t row, uint32_t len,
+                                            uint32_t l, uint32_t nxt, uint32_t QA,
+                                            Counters& K) {
+  const unsigned lane = lane_id();
+  for (uint32_t k0 = 0; k0 < len; k0 += 64u) {
+    bool valid[2];
+    uint32_t p[2], lv[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint32_t e = k0 + (uint32_t)q * 32u + lane;
+      valid[q] = e < len;
+      p[q] = valid[q] ? __ldg(&D.itgt[row + e]) : 0u;
+      lv[q] = l;
+    }
+    async_push<2>(D, B, valid, p, lv, nxt, QA, K);
+  }
+}
+
+// All threads: pushes the entries [lo, hi) of a list of (predecessor, level)
+// pairs, two per thread at a time (warps past the end skip the pass).
+__device__ __forceinline__ void async_entries(const Dev& D, Cta& B, const uint32_t* ids,
+                                              const uint32_t* lv, uint32_t lo, uint32_t hi,
+                                              bool global, uint32_t nxt, uint32_t QA,
+                                              Counters& K) {
+  for (uint32_t base = lo; base < hi; base += 2u * blockDim.x) {  // CTA-uniform
+    if (base + (threadIdx.x & ~31u) >= hi) break;  // (warp-uniform: later bases are larger)
+    bool valid[2];
+    uint32_t p[2], l[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint32_t k = base + (uint32_t)q * blockDim.x + threadIdx.x;
+      valid[q] = k < hi;
+      p[q] = valid[q] ? (global ? ldcg(&ids[k]) : ids[k]) : 0u;
+      l[q] = valid[q] ? (global ? ldcg(&lv[k]) : lv[k]) : 0u;
+    }
+    async_push<2>(D, B, valid, p, l, nxt, QA, K);
+  }
+}
+
+constexpr uint32_t AS_STEP = 0, AS_DONE = 1, AS_REBALANCE = 2;
+
+// Thread 0: releases this CTA's token, after publishing its removals and top
+// level (CTA 0 reads the totals once the token count is zero).
+__device__ __forceinline__ void async_release(const Dev& D, Cta& B) {
+  Ctrl* C = D.C;
+  if (B.a_removed) {
+    atomicAdd(&C->a_removed, B.a_removed);
+    atomicMax(&C->a_maxlev, B.a_maxlev);
+    B.a_removed = 0u;
+    B.a_maxlev = 0u;
+  }
+  fence_acq_rel();  // the counts before the release
+  atomicSub(&C->a_tokens, 1u);
+  B.a_token = 0u;
+}
+
+// Thread 0, before each step: buffer cur holds the predecessors the next step
+// pushes. A CTA with work asks for a rebalance when its removals did not fit
+// its queue or its queue holds more than max(half its threads, 2 x the
+// average share at the last rebalance): steps stay short (a step takes as long
+// as its CTA's slowest chain of loads, and one push per thread or less keeps
+// that to a single pass), and joins one when the hints (the requested
+// generation and the error flag, loaded during the previous step) show one. A
+// CTA without work publishes its counts, releases its token, and waits until
+// a rebalance is asked for or the token count is zero (the run is over). The
+// wait is bounded: spin_limit_ns without a heartbeat from a working CTA
+// (every 256 of its steps) ends the run with TRIM_ERR_TIMEOUT.
+__device__ void async_decide(const Dev& D, Cta& B, uint32_t cur, uint32_t h_req,
+                             uint32_t h_err) {
+  Ctrl* C = D.C;
+  B.aq_res[cur ^ 1u] = 0u;  // read by the previous step: the next one fills it
+  B.aq_end[cur ^ 1u] = 0u;
+  B.sh_elo = B.sh_ehi = B.sh_plo = B.sh_phi = 0u;  // the last rebalance's share is pushed
+  B.a_next = AS_STEP;
+  const uint32_t qe = B.aq_end[cur];
+  const bool over = qe > max(blockDim.x / 2u, 2u * B.a_avg);
+  if (qe != 0u || B.a_want) {
+    if ((++B.a_steps & 255u) == 0u) red_relaxed_add(&C->a_beat, 1u);
+    if (h_err != 0u) {
+      B.err = h_err;
+      B.a_next = AS_DONE;
+    } else if (B.a_want || over) {
+      atomicMax(&C->a_req, B.a_gen + 1u);
+      B.a_next = AS_REBALANCE;
+    } else if ((int)(h_req - B.a_gen) > 0) {
+      B.a_next = AS_REBALANCE;
+    }
+    return;
+  }
+  if (B.a_token) async_release(D, B);
+  uint64_t t0 = globaltimer();
+  uint32_t beat = ld_relaxed(&C->a_beat);
+  while (true) {
+    const uint32_t err = ld_relaxed(&C->err);
+    const uint32_t req = ld_relaxed(&C->a_req);
+    const uint32_t tok = ld_relaxed(&C->a_tokens);
+    const uint32_t bt = ld_relaxed(&C->a_beat);
+    if (err != 0u) {
+      B.err = err;
+      B.a_next = AS_DONE;
+      return;
+    }
+    if ((int)(req - B.a_gen) > 0) {
+      B.a_next = AS_REBALANCE;
+      return;
+    }
+    // (a CTA that asks for a rebalance holds its token until the rebalance,
+    // so a zero count means no rebalance can come)
+    if (tok == 0u) {
+      B.a_next = AS_DONE;
+      return;
+    }
+    const uint64_t now = globaltimer();
+    if (bt != beat) {
+      beat = bt;
+      t0 = now;
+    } else if (now - t0 > D.spin_limit_ns) {
+      set_error(D, TRIM_ERR_TIMEOUT, 4);
+      B.err = TRIM_ERR_TIMEOUT;
+      B.a_next = AS_DONE;
+      return;
+    }
+    __nanosleep(256);
+  }
+}
+
+// All threads, every CTA (generation g = B.a_gen): writes the entries of
+// buffer cur to the global entry list of parity g & 1; after a grid barrier
+// every CTA takes an even slice of those entries and of the pieces written
+// since the last rebalance; tokens follow the new shares and CTA 0 clears the
+// other parity's list (last read after rebalance g - 1, by every CTA before
+// this rebalance's first barrier); a second barrier publishes both before any
+// CTA writes to the lists again. Returns false on an error.
+__device__ __noinline__ bool async_rebalance(const Dev& D, Cta& B, uint32_t cur, uint32_t QA) {
+  Ctrl* C = D.C;
+  const uint32_t par = B.a_gen & 1u;
+  const uint32_t qe = B.aq_end[cur];
+  uint32_t* eid = D.ae_id + (size_t)par * D.ae_cap;
+  uint32_t* elv = D.ae_lev + (size_t)par * D.ae_cap;
+  if (threadIdx.x == 0) {
+    B.a_base = qe ? atomicAdd(&C->e_n[par], qe) : 0u;
+    // (cannot fail: a list holds every CTA's whole queue)
+    if ((uint64_t)B.a_base + qe > D.ae_cap) set_error(D, TRIM_ERR_STATE, 7);
+  }
+  __syncthreads();
+  const uint32_t base = B.a_base;
+  if ((uint64_t)base + qe <= D.ae_cap) {
+    const uint32_t* ids = dyn_smem + cur * QA;
+    const uint32_t* lv = dyn_smem + (2u + cur) * QA;
+    for (uint32_t k = threadIdx.x; k < qe; k += blockDim.x) {
+      eid[base + k] = ids[k];
+      elv[base + k] = lv[k];
+    }
+  }
+  if (!grid_barrier(D, B)) return false;
+  if (threadIdx.x == 0) {
+    const uint64_t G = gridDim.x, b = blockIdx.x;
+    const uint64_t tE = ld_relaxed(&C->e_n[par]);
+    const uint32_t p_hi = ld_relaxed(&C->oq_res);
+    const uint64_t tP = p_hi - B.a_plo;
+    B.sh_elo = (uint32_t)(b * tE / G);
+    B.sh_ehi = (uint32_t)((b + 1u) * tE / G);
+    B.sh_plo = B.a_plo + (uint32_t)(b * tP / G);
+    B.sh_phi = B.a_plo + (uint32_t)((b + 1u) * tP / G);
+    B.a_plo = p_hi;
+    const uint64_t avg = (tE + tP * kAsyncPiece) / G;
+    B.a_avg = avg < (1u << 24) ? (uint32_t)avg : (1u << 24);
+    B.aq_res[cur] = 0u;  // the queue went to the list
+    B.aq_end[cur] = 0u;
+    B.a_want = 0u;
+    B.a_gen += 1u;
+    const uint32_t busy = (B.sh_ehi > B.sh_elo || B.sh_phi > B.sh_plo) ? 1u : 0u;
+    if (busy && !B.a_token) {
+      atomicAdd(&C->a_tokens, 1u);
+      B.a_token = 1u;
+    } else if (!busy && B.a_token) {
+      async_release(D, B);
+    }
+    if (blockIdx.x == 0) {
+      C->e_n[par ^ 1u] = 0u;
+      C->a_rebalances = B.a_gen;
+    }
+  }
+  return grid_barrier(D, B);
+}
+
+// Runs the rest of the run asynchronously from round B.S.round = r0 (all
+// threads): every vertex's word is set from its counter, the pending
+// work-list entries (level r0 - 1) are pushed, one per warp, and then the
+// CTA runs steps (and rebalances) until the token count is zero. CTA 0 then
+// publishes the run's totals: alpha = top level + 1 (r0 if the tail removed
+// nothing), and one AC-4 round for each of rounds r0 .. alpha. Returns false
+// on an error.
+__device__ __noinline__ bool async_tail(const Dev& D, Cta& B) {
+  Counters K;
+  Ctrl* C = D.C;
+  const unsigned warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t QA = nw * D.sbuf_cap;  // entries per buffer: the four slices' space
+  const uint32_t r0 = B.S.round;
+  {
+    // four counters per 16-byte load where both arrays allow it
+    const bool vec = ((reinterpret_cast<uintptr_t>(D.cnt) | reinterpret_cast<uintptr_t>(D.aw)) & 15u) == 0u;
+    const uint32_t n4 = vec ? D.n >> 2 : 0u, stride = gridDim.x * blockDim.x;
+    const uint4* c4 = reinterpret_cast<const uint4*>(D.cnt);
+    ulonglong2* w2 = reinterpret_cast<ulonglong2*>(D.aw);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+      const uint4 c = __ldcg(&c4[i]);
+      w2[2u * i] = make_ulonglong2(c.x, c.y);
+      w2[2u * i + 1u] = make_ulonglong2(c.z, c.w);
+    }
+    for (uint32_t v = (n4 << 2) + blockIdx.x * blockDim.x + threadIdx.x; v < D.n; v += stride)
+      D.aw[v] = (unsigned long long)ldcg(&D.cnt[v]);
+  }
+  if (threadIdx.x == 0) {
+    B.aq_res[0] = B.aq_res[1] = 0u;
+    B.aq_end[0] = B.aq_end[1] = 0u;
+    B.sh_elo = B.sh_ehi = B.sh_plo = B.sh_phi = 0u;
+    B.a_removed = 0u;
+    B.a_maxlev = 0u;
+    B.a_token = 1u;
+    B.a_steps = 0u;
+    B.a_want = 0u;
+    B.a_gen = 0u;
+    B.a_plo = 0u;
+    B.a_avg = (B.S.e_end - B.S.e_c4) / gridDim.x;
+    if (blockIdx.x == 0) {
+      C->a_tokens = gridDim.x;
+      C->a_round = r0;
+    }
+  }
+  if (!grid_barrier(D, B, false)) return false;
+  {
+    const uint32_t ia = B.S.c4w, ib = B.S.w_end, eb = B.S.e_end;
+    for (uint32_t j = ia + warp * gridDim.x + blockIdx.x; j < ib; j += gridDim.x * nw) {
+      const uint32_t row = ldcg(&D.w4_row[j]);
+      const uint32_t eo = ldcg(&D.w4_eoff[j]);
+      const uint32_t ee = (j + 1u < ib) ? ldcg(&D.w4_eoff[j + 1u]) : eb;
+      async_piece(D, B, row, ee - eo, r0 - 1u, 0u, QA, K);
+    }
+  }
+  uint32_t cur = 0, h_req = 0, h_err = 0;
+  bool ok = true;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) async_decide(D, B, cur, h_req, h_err);
+    __syncthreads();
+    const uint32_t next = B.a_next;
+    if (next == AS_DONE) break;
+    if (next == AS_REBALANCE && !async_rebalance(D, B, cur, QA)) {
+      ok = false;
+      break;
+    }
+    if (threadIdx.x == 0) {  // hints for the next decision, in flight during the step
+      h_req = ld_relaxed(&C->a_req);
+      h_err = ld_relaxed(&C->err);
+    }
+    const uint32_t nxt = cur ^ 1u;
+    // a rebalance's share: entries of the global list, then pieces (one per warp)
+    if (B.sh_ehi > B.sh_elo) {
+      const size_t o = (size_t)((B.a_gen - 1u) & 1u) * D.ae_cap;
+      async_entries(D, B, D.ae_id + o, D.ae_lev + o, B.sh_elo, B.sh_ehi, true, nxt, QA, K);
+    }
+    for (uint32_t i = B.sh_plo + warp; i < B.sh_phi; i += nw)
+      async_piece(D, B, ldcg(&D.oq_row[i]), ldcg(&D.oq_len[i]), ldcg(&D.oq_lev[i]), nxt, QA, K);
+    async_entries(D, B, dyn_smem + cur * QA, dyn_smem + (2u + cur) * QA, 0u, B.aq_end[cur],
+                  false, nxt, QA, K);
+    cur = nxt;
+  }
+  stats_flush(D, B, K);
+  if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && ok && B.err == 0u) {
+      fence_acq_rel();  // every CTA published its counts before its last release
+      const uint32_t removed = ld_relaxed(&C->a_removed);
+      const uint32_t top = ld_relaxed(&C->a_maxlev);
+      Sched& S = B.S;
+      const uint32_t alpha = removed ? max(r0, top + 1u) : r0;
+      S.vcount[TRIM_AC4_PUSH] += alpha - r0 + 1u;
+      C->vcount[TRIM_AC4_PUSH] = S.vcount[TRIM_AC4_PUSH];
+      C->rounds = alpha;
+      C->n_dead = S.fe + removed;
+    }
+    B.S.done = 1u;
+  }
+  __syncthreads();
+  return ok && B.err == 0u;
 }
 #endif
 
@@ -2020,6 +2534,11 @@ __global__ void __launch_bounds__(512, TRIM_MIN_BLOCKS) TRIM_KERNEL(Dev D) {
       break;
     }
 #if TRIM_LOCAL
+    if (async_start(D, S)) {
+      if (!async_tail(D, B)) break;
+      fresh = false;  // done: the tail ran the rest of the run
+      continue;
+    }
     if (local_start(D, S)) {
       if (!local_stretch(D, B)) break;
       fresh = false;  // done, or the stretch's last round already ran advance()

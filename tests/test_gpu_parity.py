@@ -411,15 +411,17 @@ def test_commit_to_ac4_after_ac6_rounds():
 
 
 def test_local_rounds_match_ordinary_rounds():
-    """AC-4 with CTA-local rounds (the default once a round's pending work is
-    small) and without them (local_round_edges = 0) give the oracle's levels
-    and the same work counters, on every small workload and the hand cases
-    (a 5,000-in-edge hub overflows the local queues; chains stay local)."""
+    """AC-4 with CTA-local rounds (once a round's pending work is small, where
+    the asynchronous tail is off) and without them (local_round_edges = 0) give
+    the oracle's levels and the same work counters, on every small workload and
+    the hand cases (a 5,000-in-edge hub overflows the local queues; chains stay
+    local)."""
     P = _P()
     graphs = [cfg.config_small(i) for i in range(5)] + list(hand_cases().values())
     for g in graphs:
         lvl, st, alpha = oracle.peel(g.off, g.tgt)
         with P.Trimmer(g.off, g.tgt, flags=P.TRIM_FLAG_STATS) as t:
+            t.set_params(async_round_edges=0)
             s_local = t.run("ac4")
             check(t, lvl, st, alpha, f"local-{g.name}", s_local)
             t.set_params(local_round_edges=0)
@@ -438,7 +440,8 @@ def test_committed_stretches_end_local_rounds_before_the_scheduler_reads():
     local rounds in the scheduler kernel, which must end before the last round
     of each stretch (that round is an ordinary one, whose features the
     scheduler reads); the levels equal the oracle's, every in-edge of a removed
-    vertex is pushed exactly once, and local rounds did run."""
+    vertex is pushed exactly once, and local rounds did run (asynchronous tail
+    off)."""
     P = _P()
     for i, K, P0 in [(2, 4, 16), (2, 3, 5), (4, 2, 7), (0, 1, 3)]:
         g = cfg.config_small(i)
@@ -449,7 +452,7 @@ def test_committed_stretches_end_local_rounds_before_the_scheduler_reads():
             din = np.diff(oracle.transpose(g.off, g.tgt)[0].astype(np.int64))
             for h in HANDOVERS:
                 t.set_params(sched_commit_rounds=K, sched_recheck_rounds=P0,
-                             sched_handover=_handover(P, h))
+                             sched_handover=_handover(P, h), async_round_edges=0)
                 for mode in ("heuristic", "learned"):
                     s = t.run(mode)
                     check(t, lvl, st, alpha, f"{mode}-commit[{i}]-{h}", s)
