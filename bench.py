@@ -410,7 +410,8 @@ def sweep_variants(P, t, g, args, key, names, flush, gofs=None, label=""):
                   if len(ts) > 1 else None,
                   "params": tuned_v or "defaults",
                   "edges_per_s": g.m / (statistics.mean(ts) * 1e-3),
-                  "rounds_by_variant": st["rounds_by_variant"], "segments": st["segments"]}
+                  "rounds_by_variant": st["rounds_by_variant"], "segments": st["segments"],
+                  "async_from_round": st.get("async_round", 0)}
         print(f"# {label}{v:10s} {statistics.mean(ts):8.4f} ms  kernel {statistics.mean(ks):8.4f} ms"
               f"  {g.m / statistics.mean(ts) / 1e-3:.3e} edges/s  rounds {st['rounds_by_variant']}"
               f"  segments {st['segments']}", file=sys.stderr, flush=True)
@@ -774,6 +775,8 @@ def run_ours(args, rank, ws, local):
         "config": {"workload": wname, "n": g.n, "m": g.m, "schedule": headline,
                    "rounds": st["rounds"], "rounds_by_variant": st["rounds_by_variant"],
                    "segments": st["segments"],
+                   "async_from_round": st.get("async_round", 0),
+                   "async_rebalances": st.get("async_rebalances", 0),
                    "params": tuned or "library defaults",
                    "l2": "flushed before every step (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
