@@ -134,7 +134,7 @@ typedef struct {
                                  them when the scheduler picks a variant the running
                                  kernel lacks: TRIM_HANDOVER_*                           */
   uint32_t async_round_edges; /* AC-4 (alone or as a committed scheduled variant), from
-                                 round 8 on: once the in-edges still to push are at most
+                                 round 128 on: once the in-edges still to push are at most
                                  this many, the rest of the run is asynchronous: no
                                  rounds, each CTA pushes the rows of the vertices it
                                  removes at its own pace, and a removed vertex takes one

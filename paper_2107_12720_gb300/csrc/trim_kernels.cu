@@ -117,7 +117,7 @@ constexpr uint32_t LQ_EDGES = 1024;   // predecessors queued per CTA per round
 constexpr uint32_t LQ_ENTRIES = 256;  // removed vertices queued per CTA per round
 constexpr uint32_t LQ_DMAX = 64;      // larger in-degrees always go to the global work list
 // asynchronous AC-4 tail (see async_tail)
-constexpr uint32_t ASYNC_MIN_ROUND = 8;  // rounds before the tail may take over
+constexpr uint32_t ASYNC_MIN_ROUND = 128;  // rounds before the tail may take over
 constexpr uint32_t AQ_LOCAL_DMAX = 1024; // larger in-degrees always go to the shared queue
 #endif
 
@@ -1198,10 +1198,6 @@ void local_leave(const Dev& D, Cta& B, uint32_t b, uint32_t r) {
 // at most local_edges_max in-edges in all, none more than 256.
 __device__ __forceinline__ bool local_start(const Dev& D, const Sched& S) {
   if (D.local_edges_max == 0u || S.variant != TRIM_AC4_PUSH) return false;
-  // where the asynchronous tail may take over from round ASYNC_MIN_ROUND on,
-  // no stretch starts before it (a stretch runs until the run is over)
-  if (D.async_edges_max != 0u && !(D.flags & F_ROUND_LOG) && S.round < ASYNC_MIN_ROUND)
-    return false;
   // with the schedulers: inside a committed stretch only, whose last round
   // (the one the scheduler reads features of) runs as an ordinary round
   if ((MODES & M_SCHED) && !(S.cstop != 0u && S.round + 1u < S.cstop)) return false;
@@ -1297,7 +1293,12 @@ __device__ bool local_barrier(const Dev& D, Cta& B, uint32_t b, uint32_t r) {
     S.lbase[slot] = cur;
     S.lround += 1u;
     const uint32_t nF = (uint32_t)d, n_ovf = (uint32_t)(d >> 32) & 0xFFFFu;
-    const bool stop = (MODES & M_SCHED) && r + 1u >= S.cstop;
+    // the stretch ends before the last round of a committed stretch (the
+    // scheduler reads its features) and, where the asynchronous tail may take
+    // over, before round ASYNC_MIN_ROUND (it starts from the work list)
+    const bool stop = ((MODES & M_SCHED) && r + 1u >= S.cstop) ||
+                      (D.async_edges_max != 0u && !(D.flags & F_ROUND_LOG) && !S.mixed &&
+                       r + 1u == ASYNC_MIN_ROUND);
     if (n_ovf == 0u && (nF == 0u || !stop)) {
       local_close(D, B, nF);  // every removal of the round is in the queues
       B.lq_next = nF ? LQ_GO : LQ_DONE;
@@ -1436,7 +1437,8 @@ __device__ __noinline__ bool local_stretch(const Dev& D, Cta& B) {
 // pending work-list entries are exactly the vertices removed in round r - 1,
 // at most async_edges_max in-edges, and runs the rest of the run (with the
 // schedulers: only inside a committed stretch, as the scheduler is not
-// consulted again).
+// consulted again). Rounds before ASYNC_MIN_ROUND stay rounds (local ones
+// where they can): on graphs that peel in fewer rounds they were faster.
 __device__ __forceinline__ bool async_start(const Dev& D, const Sched& S) {
   if (D.async_edges_max == 0u || S.variant != TRIM_AC4_PUSH || S.mixed) return false;
   if ((D.flags & F_ROUND_LOG) || S.round < ASYNC_MIN_ROUND) return false;

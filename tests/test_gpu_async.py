@@ -1,6 +1,6 @@
 """The asynchronous AC-4 tail against the oracle.
 
-From round 8 on, once the in-edges still to push are few (async_round_edges),
+From round 128 on, once the in-edges still to push are few (async_round_edges),
 an AC-4 run finishes without rounds: each CTA pushes the rows of the vertices it
 removes at its own pace, and a removed vertex takes one more than the top level
 among its successors (Definition 2), carried by the pushes in a 64-bit
@@ -14,13 +14,14 @@ graphs below force that path at every other level of a chain, and with a
 import numpy as np
 import pytest
 
+import graphgen as gg
 import graphgen.configs as cfg
 import oracle
 from tests.test_gpu_parity import _confident_ac4_model, check, dev_csr, dev_csr_in, hand_cases
 
 pytestmark = pytest.mark.gpu
 
-ASYNC_MIN_ROUND = 8
+ASYNC_MIN_ROUND = 128
 
 
 def _P():
@@ -28,13 +29,14 @@ def _P():
     return P
 
 
-def broom(L=120, small=3, big=1500, mid=300, hub_at=40, hub=100_000):
+def broom(L=260, short_until=136, small=3, big=1500, mid=300, hub_at=150, hub=100_000):
     """A chain c_{L-1} -> ... -> c_0 (c_0 a sink); chain vertex c_i has k_i
-    leaf predecessors (out-degree 1, into c_i): 3 for i < 16 (the rows pending
-    when the tail takes over stay short), then 1,500 (even i: longer than the
-    shared-memory queue takes) or 300 (odd i), and 100,000 at c_hub_at. Levels:
-    c_i = i, its leaves i + 1."""
-    k = np.array([small if i < 16 else (hub if i == hub_at else (big if i % 2 == 0 else mid))
+    leaf predecessors (out-degree 1, into c_i): 3 for i < short_until (the
+    rows pending when the tail takes over, at round 128, stay short), then
+    1,500 (even i: longer than the shared-memory queue takes) or 300 (odd i),
+    and 100,000 at c_hub_at. Levels: c_i = i, its leaves i + 1."""
+    k = np.array([small if i < short_until else
+                  (hub if i == hub_at else (big if i % 2 == 0 else mid))
                   for i in range(L)], np.int64)
     leaf_tgt = np.repeat(np.arange(L, dtype=np.uint32), k)
     n = L + leaf_tgt.size
@@ -62,7 +64,8 @@ def _check_tail(s, lvl, st, alpha, label):
 
 @pytest.mark.parametrize("i", [0, 1, 2, 3, 4])
 def test_small_configs_async_equals_rounds(i):
-    """Every small workload: the tail (default) and round-synchronous AC-4
+    """Every small workload: the tail (default; it takes over at round 128 in
+    the deep cascade and the mixed graph) and round-synchronous AC-4
     (async_round_edges = 0, with and without local rounds) give the oracle's
     levels, alpha, removal count and in-edge pushes."""
     P = _P()
@@ -82,31 +85,36 @@ def test_small_configs_async_equals_rounds(i):
             assert s2["async_round"] == 0 and s2["in_edges_pushed"] == want
 
 
-@pytest.mark.parametrize("name", ["chain", "worked_example", "big_in_hub", "duplicates",
-                                  "self_loops", "edgeless", "single"])
+@pytest.mark.parametrize("name", ["long_chain", "chain", "worked_example", "big_in_hub",
+                                  "duplicates", "self_loops", "edgeless", "single"])
 def test_hand_cases_async(name):
+    """The hand cases (alpha below 128: rounds only) and a 300-vertex chain
+    (the tail takes over at round 128, one vertex per level)."""
     P = _P()
-    g = hand_cases()[name]
+    if name == "long_chain":
+        k = 300
+        g = gg.edges_from_lists(k, [[]] + [[i - 1] for i in range(1, k)])
+    else:
+        g = hand_cases()[name]
     lvl, st, alpha = oracle.peel(g.off, g.tgt)
     with P.Trimmer(g.off, g.tgt) as t:
         s = t.run("ac4")
         check(t, lvl, st, alpha, name, s)
-        if name == "chain":
-            _check_tail(s, lvl, st, alpha, name)
+        _check_tail(s, lvl, st, alpha, name)
 
 
 @pytest.mark.parametrize("block", [512, 128])
 def test_rows_spill_to_the_global_queue(block):
-    """The broom: from c_16 on every other chain vertex has a 1,501-edge G^T row
-    (beyond the shared-memory queue: 256-edge pieces in the global list, spread
-    over the CTAs by a rebalance), and c_40's 100,001 in-edges become 391
-    pieces. With 128
+    """The broom: from c_136 on every other chain vertex has a 1,501-edge G^T
+    row (beyond the shared-memory queue: 256-edge pieces in the global list,
+    spread over the CTAs by a rebalance), and c_150's 100,001 in-edges become
+    391 pieces. With 128
     threads per CTA the queue holds 1,024 entries, so rows spill more often."""
     P = _P()
     off, tgt = broom()
     lvl, st, alpha = oracle.peel(off, tgt)
-    assert alpha == 121
-    assert lvl[0] == 0 and lvl[119] == 119
+    assert alpha == 261
+    assert lvl[0] == 0 and lvl[259] == 259
     with P.Trimmer(off, tgt, flags=P.TRIM_FLAG_STATS) as t:
         t.set_params(block_threads=block)
         for rep in range(3):
@@ -137,8 +145,9 @@ def test_thresholds_and_repeated_runs():
 
 
 def test_scheduled_runs_take_the_tail_inside_committed_stretches():
-    """Heuristic and learned runs that commit to AC-4 take the tail inside the
-    committed stretch (every handover); with a round log they never do (the
+    """Heuristic and learned runs that commit to AC-4 take the tail inside a
+    committed stretch (stretches of 64, then 128 rounds: round 128 falls in the
+    second; every handover); with a round log they never do (the
     log needs rounds), and without a commit the scheduler keeps the rounds. The
     learned runs use a model that picks AC-4 with high confidence."""
     P = _P()
@@ -197,7 +206,8 @@ def test_batched_run_with_the_tail():
 
 def test_full_deep_cascade_takes_the_tail():
     """The 2^24-vertex deep cascade (alpha 2,868) in the benchmark's launch
-    shape: the tail takes over at round 8 and the levels equal the oracle's."""
+    shape: local rounds until round 127, the tail from round 128; the levels
+    equal the oracle's."""
     P = _P()
     g = cfg.config(2)
     oi_np, ti_np = oracle.transpose(g.off, g.tgt)
