@@ -34,7 +34,7 @@ def _worker(rank, ws, port, out):
 def test_two_gloo_replicas_reduce_like_the_benchmark():
     ws = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a process that may hold a CUDA context
     out = mgr.dict()
     mp.spawn(_worker, args=(ws, port, out), nprocs=ws, join=True)
     for rank in range(ws):
