@@ -484,10 +484,8 @@ trim_err_t trim_probe_atomic_rate(const uint32_t* idx, uint64_t n_idx, uint32_t*
  * stream); a stream of another device is refused with TRIM_ERR_INVALID_ARG.
  *
  * The first call on each device (with that device current) looks up the
- * array's device address and the launch shape. No call may be made while
- * cuda_stream is being captured into a CUDA graph: every call copies the
- * run's status to host memory and waits for it (see below), which a capture
- * does not allow. Every call on a device uses the same array, which keeps
+ * array's device address and the launch shape; make that first call before
+ * any stream capture. Every call on a device uses the same array, which keeps
  * the previous call's contents (the call clears what must start at zero):
  * calls whose GPU work overlaps (several streams, several host threads) race
  * on it and must be serialised by the caller. The call waits for its work on
