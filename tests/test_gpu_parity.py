@@ -612,12 +612,17 @@ def test_full_large_mixed_workload_certificate():
     """The large mixed workload at full size (R-MAT scale 26 union a 2^25-vertex
     planted block: n = 100.7M, m = 1.22e9, alpha = 10,004) in the launch shape the
     benchmark uses, with the fixed AC-4 variant and both schedulers (the learned
-    one is the benchmark's headline schedule on this graph). Checked with the oracle's certificate, which holds for exactly
-    one status/level assignment (the trimming result), plus the planted block's
+    one is the benchmark's headline schedule on this graph). Every vertex is
+    compared with the oracle's peel (given the workload's G^T, which
+    test_input_transpose_equals_the_oracles pins to the oracle's own
+    transpose), and the result also passes the oracle's certificate, which
+    holds for exactly one status/level assignment, and the planted block's
     closed form (C and R live, chain vertices at their chain position)."""
     P = _P()
     from paper_2107_12720_gb300 import scheduler
     u = cfg.config(4)
+    want_lvl, want_st, alpha = oracle.peel(u.off, u.tgt, gg.transpose(u.off, u.tgt))
+    assert alpha == 10004
     off, tgt = dev_csr(u)
     rmat_n = u.meta["rmat_n"]
     nC, nR, nT, chains = u.meta["block"]
@@ -625,6 +630,7 @@ def test_full_large_mixed_workload_certificate():
         t.set_model(scheduler.load_blob())
         for v in ["ac4", "heuristic", "learned"]:
             s = t.run(v)
+            check(t, want_lvl, want_st, alpha, v, s)
             lvl = t.level(device=False)
             st = t.status(device=False)
             assert oracle.certificate(u.off, u.tgt, lvl, st) == -1, v
