@@ -161,7 +161,12 @@ typedef struct {
   uint32_t rounds;          /* alpha: number of peeling steps that removed something      */
   uint32_t n_dead;          /* vertices removed                                          */
   float device_ms;          /* trim time between events around the device work          */
-  uint64_t edges_inspected; /* TRIM_FLAG_STATS: out-edges read by AC-6/AC-3 scans         */
+  uint64_t edges_inspected; /* TRIM_FLAG_STATS: out-edge targets read by AC-6/AC-3 scans.
+                               Scans read targets in groups (4 per thread step, up to 32
+                               per warp step) and a scan that resumes after its support
+                               reads again the targets its last group loaded past it, so
+                               the count can exceed m for AC-6, whose logical inspections
+                               are at most m (Section 8)                                */
   uint64_t in_edges_pushed; /* TRIM_FLAG_STATS: in-edges walked by AC-4 (atomics issued)   */
   uint64_t candidates;      /* TRIM_FLAG_STATS: AC-6 supporting-set members re-scanned     */
   uint64_t live_swept;      /* TRIM_FLAG_STATS: AC-3 live-list entries visited             */
