@@ -63,3 +63,26 @@ def test_input_transpose_equals_the_oracles():
     for g in graphs:
         a, b = gg.transpose(g.off, g.tgt), oracle.transpose(g.off, g.tgt)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), g
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the oracle timed on the host cores, no GPU
+    needed) prints exactly one JSON line with the keys the benchmark contract
+    asks of that arm, on the workload it was given."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", "0",
+                        "--steps", "3", "--warmup", "1"], cwd=root, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 3 and d["warmup"] == 1
+    assert d["unit"] == "edges/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["config"]["n"] == 100000 and d["config"]["workload"].startswith("planted_trim")
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "edges/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
