@@ -86,3 +86,14 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "edges/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_measured_peak_or_fallback(tmp_path):
+    good = tmp_path / "good.json"
+    good.write_text('{"hbm_gbs": 6777.6, "bf16_tflops": 1900}')
+    assert bench.measured_peaks(str(good)) == (6777.6, "measured")
+    for text in ['{"bf16_tflops": 1900}', '{"hbm_gbs": null}', '{"hbm_gbs": 0}', "not json"]:
+        bad = tmp_path / "bad.json"
+        bad.write_text(text)
+        assert bench.measured_peaks(str(bad)) == (6800.0, "fallback"), text
+    assert bench.measured_peaks(str(tmp_path / "absent.json")) == (6800.0, "fallback")
