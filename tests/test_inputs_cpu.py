@@ -129,3 +129,55 @@ def test_graphs_do_not_depend_on_the_thread_count():
         assert r.returncode == 0, r.stderr[-2000:]
         digests.add(r.stdout.strip())
     assert len(digests) == 1
+
+
+def implicit_rows(seed, salt, nC, nR, nT, c_k, r_k, t_sinks, t_k, n_chains):
+    """Successor lists of the implicit planted graph as include/trim.h defines
+    them (written from that definition, not from the generator's source)."""
+    def word(v, i):
+        key = mix64(seed ^ mix64((salt + v + GAMMA) & M64))
+        return mix64((key + (i + 1) * GAMMA) & M64)
+
+    def below(w, k):
+        return (w * k) >> 64
+
+    def draw(v, lo, hi):
+        return lo + below(word(v, 0), hi - lo + 1)
+
+    out = []
+    for v in range(nC + nR + nT):
+        if v < nC:
+            k = draw(v, *c_k)
+            succ = [below(word(v, 1 + j), nC) for j in range(k)]
+        elif v < nC + nR:
+            k = draw(v, *r_k)
+            succ = [below(word(v, 1 + j), nC if j == 0 else nC + nR) for j in range(k)]
+        else:
+            rank = v - nC - nR
+            if n_chains == 0:
+                k = 0 if rank < t_sinks else draw(v, *t_k)
+                succ = [nC + nR + below(word(v, 1 + j), rank) for j in range(k)]
+            else:
+                pos = rank // n_chains
+                k = 0 if pos == 0 else 1 + draw(v, *t_k)
+                succ = [v - n_chains if j == 0 else
+                        nC + nR + below(word(v, 1 + j), pos * n_chains) for j in range(k)]
+        out.append(succ)
+    return out
+
+
+@pytest.mark.parametrize("params", [
+    dict(seed=9, salt=0, nC=50, nR=40, nT=60, c_k=(4, 4), r_k=(1, 4), t_sinks=5, t_k=(1, 4),
+         n_chains=0),
+    dict(seed=3, salt=123, nC=40, nR=80, nT=280, c_k=(8, 8), r_k=(1, 15), t_sinks=0,
+         t_k=(0, 14), n_chains=8)])
+def test_implicit_definition_equals_the_generated_graph(params):
+    """The successor function that trim_create_implicit documents gives, row by
+    row once sorted and deduplicated, the graph graphgen materialises for the
+    oracle."""
+    g = gg.planted(params["seed"], params["nC"], params["nR"], params["nT"], c_k=params["c_k"],
+                   r_k=params["r_k"], t_sinks=params["t_sinks"], t_k=params["t_k"],
+                   n_chains=params["n_chains"], salt=params["salt"])
+    want = implicit_rows(**params)
+    for v, r in rows(g):
+        assert r.tolist() == sorted(set(want[v])), v
